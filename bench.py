@@ -58,8 +58,12 @@ def _args():
     p.add_argument("--max-batch", type=int, default=0,
                    help="queries per micro-batch (0: sized by the frontier budget)")
     p.add_argument("--items", type=int, default=0, help="database size (0: the workload's)")
+    p.add_argument("--scratch-gb", type=float, default=0.0,
+                   help="device scratch budget of a query call in GB (0: the library's default)")
     p.add_argument("--sweep-cutover", default="", help="comma list of cutover levels to time too")
     p.add_argument("--cpu-sample", type=int, default=0, help="oracle sample size (0: auto)")
+    p.add_argument("--parity-sample", type=int, default=256,
+                   help="queries checked against the oracle's FP64 brute force")
     p.add_argument("--layout", default="tree", choices=["tree", "prefix"],
                    help="tree: a row per pool; prefix: Eq. 1's cumulative sums restarted per "
                         "block of 2^c items (--prefix-level c), the blocks scored by the GEMM")
@@ -68,6 +72,8 @@ def _args():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--no-stream", action="store_true", help="skip the streaming-setting run")
+    p.add_argument("--no-e2e", action="store_true",
+                   help="skip the end-to-end calls (small profiling runs)")
     p.add_argument("--serve-rates", default="50000,400000,0",
                    help="offered request rates for the serving run (0: all at once)")
     return p.parse_args()
@@ -166,6 +172,19 @@ class Clocks:
                 "sm_max_mhz": max(mx) if mx else None,
                 "power_w_median": statistics.median(pw) if pw else None,
                 "samples": len(rows), "in_timed_region": bool(inside), "reasons": reasons}
+
+
+def _cpu_model() -> str:
+    """The host CPU's model name (lscpu), else the machine type."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return f"{line.split(':', 1)[1].strip()} ({platform.machine()}, {os.cpu_count()} cpus)"
+    except Exception:
+        pass
+    return f"{platform.processor() or platform.machine()} ({os.cpu_count()} cpus)"
 
 
 def _traffic_record(kernel: str):
@@ -269,8 +288,8 @@ def streaming_run(gt, ds, dtype, rho, chunk=100, n_check=256, seed=0):
     chunk, until the whole database is in.  Reports the index build time, the
     mean insertion time per point, the mean query time, and precision and
     recall on a sample of the queries, each against the exhaustive scan
-    (gt_exhaustive, the paper's Exh) restricted to the items present when the
-    query ran."""
+    (gt_exhaustive_tree, the paper's Exh over the tree's items) restricted to
+    the items present when the query ran."""
     import torch
     N = ds.F.shape[0]
     n0 = int(0.8 * N)
@@ -328,9 +347,47 @@ def streaming_run(gt, ds, dtype, rho, chunk=100, n_check=256, seed=0):
             "mqt_ms": round(float(np.mean(t_q)), 3), "mqt_p99_ms": round(float(np.percentile(t_q, 99)), 3),
             "checked_queries": len(ks), "mp": 1.0 if tp + fp == 0 else round(tp / (tp + fp), 6),
             "mr": 1.0 if tp + fn == 0 else round(tp / (tp + fn), 6),
-            "reference": "gt_exhaustive on the final database, ids filtered to the snapshot",
+            "reference": "gt_exhaustive_tree on the final database, ids filtered to the snapshot",
             "timing": "host wall clock per public-API call (gt_insert of a host chunk; gt_query of one "
                       "host query with a host CSR result)"}
+
+
+def _e2e_calls(a, tree, Q, rho, B, stream, flush):
+    """End to end through the C ABI: pinned host inputs, CSR written into
+    caller-owned pinned host buffers (gt_query_into), every step's copies
+    inside the timed region; and gt_query with a library-allocated host CSR."""
+    import torch
+    _note("end-to-end calls")
+    Qh = torch.from_numpy(Q).pin_memory()
+    rh = torch.from_numpy(rho).pin_memory()
+    r = tree.query(Qh, rh, dtype=a.dtype, cutover=a.cutover, stream=stream)
+    offs_h = torch.empty(B + 1, dtype=torch.int64).pin_memory()
+    ids_h = torch.empty(max(1, int(r.ids.size * 1.5)), dtype=torch.int32).pin_memory()
+    offs_np, ids_np = offs_h.numpy(), ids_h.numpy()
+    torch.cuda.synchronize()
+    e2e_t, e2e_lib_t, d2h = [], [], 0
+    for _ in range(max(2, a.steps // 2)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        n_res = tree.query_into(Qh, rh, offs_np, ids_np, dtype=a.dtype, cutover=a.cutover,
+                                stream=stream)
+        e2e_t.append(time.perf_counter() - t1)
+        d2h = offs_np.nbytes + n_res * 4
+        flush.zero_()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        r = tree.query(Qh, rh, dtype=a.dtype, cutover=a.cutover, stream=stream)
+        e2e_lib_t.append(time.perf_counter() - t1)
+    e2e = {"value": round(B / statistics.mean(e2e_t), 1), "unit": UNIT,
+           "h2d_bytes_per_step": int(Qh.numel() * 4 + rh.numel() * 4),
+           "d2h_bytes_per_step": int(d2h),
+           "call": "gt_query_into, pinned host inputs and caller-owned pinned host CSR"}
+    e2e_library_csr = {"value": round(B / statistics.mean(e2e_lib_t), 1), "unit": UNIT,
+                       "call": "gt_query with a library-allocated (pageable) host CSR"}
+    assert np.array_equal(r.offsets, offs_np) and np.array_equal(r.ids, ids_np[:n_res])
+    host_result = r
+    return e2e, e2e_library_csr, host_result
 
 
 def run_reference(a):
@@ -365,6 +422,7 @@ def run_reference(a):
             "config": {"workload": a.workload, "N": int(ds.F.shape[0]), "d": int(ds.F.shape[1]),
                        "queries_per_step": per_step, "rho": a.rho},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "cpu_model": _cpu_model(),
                              "sample": f"Algorithm 1 (FP64 cumulative sums) on {per_step} random "
                                        f"queries per step, rho={a.rho}; cumulative-sum build "
                                        "not timed"},
@@ -413,7 +471,6 @@ def main():
         tree = gt.Tree(Fd, capacity=N + 65536)
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
-    del Fd
     Qd = torch.from_numpy(Q).to(dev)
     rd = torch.from_numpy(rho).to(dev)
     stream = torch.cuda.current_stream()
@@ -431,9 +488,12 @@ def main():
         _note(f"autotuning on {ns} queries")
         tune = tree.autotune(Qd[:ns], rd[:ns], dtype=a.dtype, stream=stream)
 
+    scratch = int(a.scratch_gb * 1e9)
+
     def step(**kw):
         return tree.query(Qd, rd, dtype=a.dtype, cutover=a.cutover, results_on_device=True,
-                          stream=stream, subtract=a.subtract, max_batch=a.max_batch, **kw)
+                          stream=stream, subtract=a.subtract, max_batch=a.max_batch,
+                          scratch_bytes=scratch, **kw)
 
     _note("timed steps")
     clocks = Clocks()
@@ -471,15 +531,31 @@ def main():
     gb = st0["gathered_bytes"]
     g_ach = gb / (gather_ms * 1e-3) / 1e9 if gather_ms > 0 else 0.0
     tr = _traffic_record("gather_prefix" if pre else "gather")
+    # Rows of popular pools are read by many queries and partly served from L2,
+    # so the algorithmic row bytes per second can exceed the copy peak.  The
+    # fraction is therefore taken on DRAM bytes (the algorithmic bytes times
+    # the DRAM/algorithmic ratio of an ncu capture of the same kernels on a
+    # small case, recorded with its command in profiles/traffic.json); the
+    # algorithmic rate is reported beside it.
+    ratio = tr["dram_bytes_per_algorithmic_byte"] if tr else None
+    traffic = ratio * gb / g_launches if ratio else None
+    g_dram = g_ach * ratio if ratio else None
     roof_gather = {"kernel": "gather (k_ring modes 5, 6: the prefix splits below the GEMM level)" if pre
                    else "gather (k_ring / k_level: the levels below the cutover and the items)",
                    "bound": "hbm",
-                   "achieved": round(g_ach, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                   "frac": round(g_ach / peaks["hbm_gbs"], 4),
+                   "achieved": round(g_dram if ratio else g_ach, 1), "peak": peaks["hbm_gbs"],
+                   "unit": "GB/s",
+                   "frac": round((g_dram if ratio else g_ach) / peaks["hbm_gbs"], 4),
+                   "basis": "DRAM bytes (algorithmic bytes x the DRAM/algorithmic ratio of "
+                            f"{tr.get('case', 'an ncu capture')}) per CUDA-event second" if ratio else
+                            "algorithmic bytes (no DRAM record for the current kernel source)",
+                   "achieved_algorithmic": round(g_ach, 1),
+                   "frac_algorithmic": round(g_ach / peaks["hbm_gbs"], 4),
+                   "dram_per_algorithmic_byte": ratio,
                    "peak_source": f"hbm_gbs of {peaks_src}",
                    "algorithmic_bytes_per_launch": gb / g_launches,
                    "avg_launch_ms": gather_ms / g_launches,
-                   "traffic": (tr["dram_bytes_per_algorithmic_byte"] * gb / g_launches) if tr else None}
+                   "traffic": traffic}
     roof_dense = None
     if km["dense"] > 0 and st0["cutover"] >= 0:
         # algorithmic: 2 d FLOP per (query, pool) score (the kernel's K is d
@@ -497,7 +573,8 @@ def main():
                                      f"frac_of_burst against bf16_tflops",
                       "algorithmic_flops_per_launch": flops / n_l,
                       "avg_launch_ms": km["dense"] / n_l,
-                      "traffic": (trd["dram_bytes_per_flop"] * flops / n_l) if trd else None}
+                      "traffic": (trd["dram_bytes_per_flop"] * flops / n_l) if trd else None,
+                      "traffic_source": trd.get("case") if trd else None}
     if roof_dense and km["dense"] > gather_ms:
         roof, roof_other = roof_dense, roof_gather
     else:
@@ -537,8 +614,15 @@ def main():
                                            "gathered_tests_per_query": s["gathered_tests"] / B,
                                            "kernel_ms": s["kernel_ms"]}
         try:
-            qps, s = timed(lambda: tree.exhaustive(Qd, rd, results_on_device=True, stream=stream))
-            comparators["exhaustive_gemm_bf16"] = {"value": round(qps, 1), "unit": UNIT}
+            # the paper's Exh: every (query, item) pair, over the database's rows
+            # as the caller holds them (gt_exhaustive: the rows are quantised to
+            # BF16 inside each call, then one tcgen05 GEMM with the bound-checked
+            # threshold and the FP64 recheck; no tree)
+            qps, s = timed(lambda: gt.exhaustive(Fd, Qd, rd, results_on_device=True, stream=stream))
+            comparators["exhaustive_gemm_bf16"] = {
+                "value": round(qps, 1), "unit": UNIT, "call": "gt_exhaustive over the FP32 rows "
+                "on the device (BF16 copy made inside the call)", "rechecks": s["rechecks"],
+                "results": s["results"]}
         except gt.GTError as e:
             comparators["exhaustive_gemm_bf16"] = {"unavailable": str(e)}
         # the paper's Our-Max: pools by element-wise maximum (Sec. 2), tuned the
@@ -588,40 +672,13 @@ def main():
             "tree_device_gb": round(rows_tree * stride_ * 7 / 1e9, 2)}
         ptree.close()
         torch.cuda.empty_cache()
+    del Fd
 
-    _note("end-to-end calls")
-    # end to end through the C ABI: pinned host inputs, CSR written into
-    # caller-owned pinned host buffers (gt_query_into), every step's copies
-    # inside the timed region
-    Qh = torch.from_numpy(Q).pin_memory()
-    rh = torch.from_numpy(rho).pin_memory()
-    r = tree.query(Qh, rh, dtype=a.dtype, cutover=a.cutover, stream=stream)
-    offs_h = torch.empty(B + 1, dtype=torch.int64).pin_memory()
-    ids_h = torch.empty(max(1, int(r.ids.size * 1.5)), dtype=torch.int32).pin_memory()
-    offs_np, ids_np = offs_h.numpy(), ids_h.numpy()
-    torch.cuda.synchronize()
-    e2e_t, e2e_lib_t, d2h = [], [], 0
-    for _ in range(max(2, a.steps // 2)):
-        flush.zero_()
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        n_res = tree.query_into(Qh, rh, offs_np, ids_np, dtype=a.dtype, cutover=a.cutover,
-                                stream=stream)
-        e2e_t.append(time.perf_counter() - t1)
-        d2h = offs_np.nbytes + n_res * 4
-        flush.zero_()
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        r = tree.query(Qh, rh, dtype=a.dtype, cutover=a.cutover, stream=stream)
-        e2e_lib_t.append(time.perf_counter() - t1)
-    e2e = {"value": round(B / statistics.mean(e2e_t), 1), "unit": UNIT,
-           "h2d_bytes_per_step": int(Qh.numel() * 4 + rh.numel() * 4),
-           "d2h_bytes_per_step": int(d2h),
-           "call": "gt_query_into, pinned host inputs and caller-owned pinned host CSR"}
-    e2e_library_csr = {"value": round(B / statistics.mean(e2e_lib_t), 1), "unit": UNIT,
-                       "call": "gt_query with a library-allocated (pageable) host CSR"}
-    assert np.array_equal(r.offsets, offs_np) and np.array_equal(r.ids, ids_np[:n_res])
-    host_result = r
+    e2e = e2e_library_csr = host_result = None
+    if a.no_e2e:
+        a.no_cpu = True       # the oracle checks the end-to-end call's result
+    else:
+        e2e, e2e_library_csr, host_result = _e2e_calls(a, tree, Q, rho, B, stream, flush)
 
     cpu = None
     parity = None
@@ -633,15 +690,30 @@ def main():
         qs.sort()
         index = oracle.Index(ds.F, threads=threads)
         ref = index.query(Q[qs], rho[qs], threads=threads)
+        # the same oracle on one thread (the paper does not state its threads)
+        q1 = qs[: min(len(qs), 64)]
+        ref1 = index.query(Q[q1], rho[q1], threads=1)
         index.close()
         cpu = {"value": round(len(qs) / ref.seconds, 2), "unit": UNIT, "cores": threads,
-               "kind": "oracle",
+               "kind": "oracle", "cpu_model": _cpu_model(),
                "sample": f"Algorithm 1 (FP64 cumulative sums) on {len(qs)} of the {B} queries, "
-                         f"rho={a.rho}; cumulative-sum build not timed"}
-        ok = all(np.array_equal(ref.neighbours(i), host_result.neighbours(int(q)))
-                 for i, q in enumerate(qs))
-        parity = {"queries": int(len(qs)), "identical": bool(ok),
-                  "oracle_ambiguous": int(ref.ambiguous.sum())}
+                         f"rho={a.rho}; cumulative-sum build not timed",
+               "one_thread": {"value": round(len(q1) / ref1.seconds, 2), "unit": UNIT, "cores": 1,
+                              "sample": f"the first {len(q1)} of those queries"}}
+        # parity against the definition: the oracle's FP64 brute force on a
+        # bounded sample (every item of the database against each query)
+        qb = np.random.default_rng(3).choice(B, min(a.parity_sample, B), replace=False)
+        qb.sort()
+        bf = oracle.brute_force(ds.F, Q[qb], rho[qb], threads=threads)
+        ok = all(np.array_equal(bf.neighbours(i), host_result.neighbours(int(q)))
+                 for i, q in enumerate(qb))
+        ok_alg1 = all(np.array_equal(ref.neighbours(i), host_result.neighbours(int(q)))
+                      for i, q in enumerate(qs))
+        parity = {"queries": int(len(qb)), "identical": bool(ok), "oracle": "brute_force (FP64)",
+                  "oracle_ambiguous": int(bf.ambiguous.sum()),
+                  "brute_force_seconds": round(bf.seconds, 2),
+                  "algorithm1": {"queries": int(len(qs)), "identical": bool(ok_alg1),
+                                 "decisions_outside_its_rounding_bound": int(ref.ambiguous.sum())}}
 
     # the serving run inserts rows, so it comes after every exactness check
     serving = None

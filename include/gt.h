@@ -70,8 +70,22 @@ typedef struct gt_tree gt_tree; /* opaque, library-owned device state */
  *   GT_POOL_MAX  the element-wise maximum of the members (Sec. 2, pooling
  *                by maximum; with non-negative entries q.y is at least the
  *                best member's score, so the same pruning holds).  Both
- *                children of every kept pool are tested: no subtraction. */
-typedef enum gt_pooling { GT_POOL_SUM = 0, GT_POOL_MAX = 1 } gt_pooling;
+ *                children of every kept pool are tested: no subtraction.
+ *   GT_POOL_MAXMIN  for descriptors with negative entries (Sec. 2 pools such
+ *                data by element-wise maximum and minimum).  Each row f is
+ *                stored split as [max(f, 0), max(-f, 0)] (2d non-negative
+ *                entries) and the pools are element-wise maxima of the split
+ *                rows, i.e. [max(M, 0), max(-m, 0)] for the members' maximum
+ *                M and minimum m; a query q is split the same way.  A pool's
+ *                split score q+.max(M, 0) + q-.max(-m, 0) bounds every
+ *                member's q.f from above, so the same pruning holds; at an
+ *                item the split score exceeds q.f by its cross terms, so
+ *                every item it keeps is decided by an FP64 dot product of the
+ *                signed q and f (no item is accepted on a bound).  Entries
+ *                may be negative (non-finite ones are still GT_EDOMAIN);
+ *                d <= 1024; the dense cutover level must be >= 1 and
+ *                gt_exhaustive_tree and the server are not available. */
+typedef enum gt_pooling { GT_POOL_SUM = 0, GT_POOL_MAX = 1, GT_POOL_MAXMIN = 2 } gt_pooling;
 
 /* How the pools are stored.
  *   GT_LAYOUT_TREE    one row per pool of every level (about 2N rows per
@@ -182,8 +196,11 @@ typedef struct gt_csr {
  * made by summing members (Eq. 1 gives the same pools as differences of
  * cumulative sums).  Level 0 is the (optionally permuted) items; level h+1
  * row j is the FP32 sum of level-h rows 2j and 2j+1.  Requires 1 <= N <
- * 2^31 and 1 <= d <= 2048.  Entries are checked: GT_EDOMAIN if any is
- * negative or not finite.  *out receives a new handle (free with gt_free). */
+ * 2^31 and 1 <= d <= 2048 (d <= 1024 for GT_POOL_MAXMIN).  Entries are
+ * checked: GT_EDOMAIN if any is negative (allowed with GT_POOL_MAXMIN) or
+ * not finite.  *out receives a new handle (free with gt_free).  The stored
+ * rows (gt_read_rows, gt_dense_scores, gt_pair_bounds) of a GT_POOL_MAXMIN
+ * tree are the split rows, 2d entries wide. */
 gt_status gt_build(const float *F, int64_t N, int32_t d, const gt_build_opts *opts,
                    gt_tree **out);
 /* A GT_LAYOUT_PREFIX tree (opts->layout) is queried by gt_query and
@@ -226,13 +243,34 @@ gt_status gt_query_into(gt_tree *t, const float *Q, int64_t B, const float *rho,
                         const gt_query_opts *opts, int64_t *offsets, int32_t *ids, int64_t ids_cap,
                         int64_t *n_results);
 
-/* Exhaustive search (the paper's Exh comparator, Sec. 4): score every
- * (query, item) pair of the tree's items with a dense tensor-core GEMM and
- * return the same exact sets as gt_query (bound-checked threshold, FP64
- * recheck near rho).  Uses only the tree's level-0 rows.  opts->dtype selects
- * the GEMM input format (GT_BF16; GT_F32 is scored as BF16 too). */
-gt_status gt_exhaustive(gt_tree *t, const float *Q, int64_t B, const float *rho,
-                        const gt_query_opts *opts, gt_csr *out);
+/* Exhaustive search over a database the caller holds (the paper's Exh
+ * comparator, Sec. 4 and Table 1: every query is compared with every item).
+ * For each of the B queries (B x d) it returns {i : q.f_i >= rho[q]} over the
+ * N rows of F (N x d, FP32, entries >= 0), as CSR lists of row numbers of F,
+ * ascending - the same exact sets gt_query returns for a tree built over F.
+ *  - Method: the rows of F are rounded once into a BF16 copy (and padded into
+ *    an FP32 copy for the recheck); a tensor-core GEMM scores every (query,
+ *    item) pair in FP32; a pair whose rigorous upper bound is below rho is
+ *    dropped, one whose lower bound reaches rho is kept, and the few in
+ *    between are settled in FP64 from the FP32 rows.  No tree is built.
+ *  - F, Q and rho may each be host or device memory; the caller keeps them.
+ *  - The library keeps, per device, the storage of the two row copies and of
+ *    the search's lists between calls (about 6 d N bytes plus the result
+ *    lists), reused by the next call; calls from several threads are
+ *    serialised.
+ *  - opts as for gt_query; dtype and cutover are ignored (the GEMM reads BF16
+ *    rows, the scan has no levels).
+ *  - Errors: GT_EINVAL for N outside [1, 2^31), d outside [1, 2048], a null
+ *    pointer or no tensor-core path; GT_EDOMAIN for a negative or non-finite
+ *    entry of F or Q; GT_ENOMEM when the row copies do not fit. */
+gt_status gt_exhaustive(const float *F, int64_t N, int32_t d, const float *Q, int64_t B,
+                        const float *rho, const gt_query_opts *opts, gt_csr *out);
+
+/* gt_exhaustive over the items of a built tree (its level-0 rows; the ids
+ * are the tree's, as for gt_query).  Not available for a prefix-layout
+ * tree, which keeps no BF16 item rows. */
+gt_status gt_exhaustive_tree(gt_tree *t, const float *Q, int64_t B, const float *rho,
+                             const gt_query_opts *opts, gt_csr *out);
 
 /* Result of gt_autotune: the choices and the device milliseconds of a query
  * batch measured for each candidate (0 where not tried). */
@@ -329,10 +367,19 @@ gt_status gt_pair_bounds(gt_tree *t, int32_t level, int32_t dtype, const float *
  *    query q's ids at ids[offsets[q] .. offsets[q+1]), ascending.
  *  - *n_results receives the number of neighbours; if it exceeds ids_cap
  *    the call returns GT_EOVERFLOW without writing ids (call again with a
- *    larger buffer).  GT_EOVERFLOW is also returned when one query's frontier
- *    does not fit the fixed array.
- *  - The first call on a device looks up the array's device address; make
- *    that first call before any stream capture.
+ *    larger buffer).
+ *  - Fixed limits of the array: 256 queries per call; rows of at most 2048
+ *    entries; 262,144 neighbours per call in all; per micro-batch 65,536 leaf
+ *    pairs awaiting the FP64 recheck and about 1.8M (query, pool) pairs in
+ *    each of two frontier lists.  A micro-batch whose frontier or recheck
+ *    list overflows is re-run with half the queries.  GT_EOVERFLOW is
+ *    returned (*n_results then 0) when the call's neighbours exceed 262,144
+ *    (split the queries over more calls) or when one query's frontier alone
+ *    does not fit.
+ *  - The tree's device (the one current at gt_build) must be current
+ *    (GT_EINVAL otherwise).  The first call on a device looks up the array's
+ *    device address and keeps it; make that first call before any stream
+ *    capture, and make no call on a device after cudaDeviceReset of it.
  *  - All calls share the array and see the previous call's leftovers (each
  *    call clears what it needs): calls that overlap on the GPU - other
  *    streams, other threads - race and must not be made.
@@ -390,6 +437,16 @@ gt_status gt_server_poll(gt_server *s, int64_t max_queries, int64_t *n_done, int
                          int64_t *offsets, int32_t *ids, int64_t ids_cap, int64_t *n_snapshot);
 gt_status gt_server_get_stats(const gt_server *s, gt_server_stats *out);
 void gt_server_free(gt_server *s);
+
+/* Failure detection (the bounded device waits): every wait of the gather
+ * kernels on their bulk copies gives up after 1 s, raises a status word that
+ * the call reads, and the call returns GT_ETIMEOUT with no results instead of
+ * leaving a kernel waiting.  To test that path without a fault, on != 0 makes
+ * the ring-fed gather kernels of later calls on tree t start no copy, so
+ * their first wait runs out at once with nothing in flight; 0 restores normal
+ * operation.  The tree's rows are not touched.  The paper has no counterpart
+ * (its implementation runs on a CPU). */
+gt_status gt_set_wait_expiry(gt_tree *t, int32_t on);
 
 int64_t gt_size(const gt_tree *t);        /* current N */
 int32_t gt_dim(const gt_tree *t);         /* d */

@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -222,6 +223,56 @@ gt_status grow(gt_tree *t, int64_t cap) {
   return GT_OK;
 }
 
+// gt_exhaustive's scan contexts, one per device: a tree of level 0 alone
+// (FP32 and BF16 rows of the items in input order) that each call rewrites
+// from the caller's rows.  Its row storage, workspace and captured graphs are
+// kept between calls; a call with another width d starts a fresh context.
+constexpr int kMaxDevices = 64;
+std::mutex g_scan_mutex;
+gt_tree *g_scan[kMaxDevices] = {nullptr};
+
+gt_status scan_context(int dev, int64_t N, int32_t d, gt_tree **out) {
+  gt_tree *&x = g_scan[dev];
+  if (x && x->d != d) {
+    gt_free(x);
+    x = nullptr;
+  }
+  if (!x) {
+    x = new gt_tree();
+    x->d = d;
+    x->d_in = d;
+    x->stride = ((int64_t)d + 63) / 64 * 64;
+    x->formats = (1u << GT_F32) | (1u << GT_BF16);
+    x->device = dev;
+    cudaDeviceGetAttribute(&x->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaMalloc(&x->flags, 64 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(x->flags, 0, 64 * sizeof(int));
+    if (e != cudaSuccess || x->sm_count <= 0) {
+      gt_free(x);
+      x = nullptr;
+      return e != cudaSuccess ? cuda_error(e, "scan context") : set_error(GT_ECUDA, "no CUDA device");
+    }
+  }
+  if (N > x->cap) {
+    free_tree_storage(x);
+    x->cap = 0;
+    const size_t n = (size_t)N * (size_t)x->stride;
+    GT_CUDA(cudaMalloc(&x->rows32, n * sizeof(float)));
+    GT_CUDA(cudaMalloc(&x->rows16, n * 2));
+    GT_CUDA(cudaMalloc(&x->perm, (size_t)N * sizeof(int32_t)));
+    x->cap = N;
+  }
+  // one level: the items (every row is rewritten in full, padding included)
+  x->N = N;
+  x->L = 0;
+  x->Lcap = 0;
+  x->lvl_off[0] = 0;
+  x->lvl_off[1] = x->cap;
+  x->total_rows = x->cap;
+  *out = x;
+  return GT_OK;
+}
+
 }  // namespace
 }  // namespace gt
 
@@ -242,8 +293,10 @@ gt_status gt_build(const float *F, int64_t N, int32_t d, const gt_build_opts *op
   if (opts) o = *opts;
   const int64_t cap = std::max<int64_t>(N, o.capacity);
   if (cap >= ((int64_t)1 << 31)) return set_error(GT_EINVAL, "capacity must be < 2^31");
-  if (o.pooling != GT_POOL_SUM && o.pooling != GT_POOL_MAX)
+  if (o.pooling != GT_POOL_SUM && o.pooling != GT_POOL_MAX && o.pooling != GT_POOL_MAXMIN)
     return set_error(GT_EINVAL, "unknown pooling");
+  const bool split = o.pooling == GT_POOL_MAXMIN;
+  if (split && d > 1024) return set_error(GT_EINVAL, "GT_POOL_MAXMIN needs d <= 1024 (rows are 2d wide)");
   if (o.layout != GT_LAYOUT_TREE && o.layout != GT_LAYOUT_PREFIX)
     return set_error(GT_EINVAL, "unknown layout");
   const bool pre = o.layout == GT_LAYOUT_PREFIX;
@@ -258,9 +311,12 @@ gt_status gt_build(const float *F, int64_t N, int32_t d, const gt_build_opts *op
   prepare_level_kernels();
   gt_tree *t = new gt_tree();
   t->N = N;
-  t->d = d;
+  // signed rows are stored split, [max(f, 0), max(-f, 0)]: 2d entries
+  t->d_in = d;
+  t->d = split ? 2 * d : d;
+  t->split_sign = split;
   t->L = top_level(N);
-  t->stride = ((int64_t)d + 63) / 64 * 64;
+  t->stride = ((int64_t)t->d + 63) / 64 * 64;
   if (pre) {
     // the formats of the prefix rows: BF16 always, FP32 on request
     t->formats = (1u << GT_BF16) | (o.formats & (1u << GT_F32));
@@ -269,10 +325,12 @@ gt_status gt_build(const float *F, int64_t N, int32_t d, const gt_build_opts *op
   } else {
     t->formats = (1u << GT_F32) | (o.formats ? o.formats : ((1u << GT_BF16) | (1u << GT_FP8)));
   }
-  t->pooling = o.pooling;
+  // split signed rows are pooled by element-wise maximum
+  t->pooling = split ? GT_POOL_MAX : o.pooling;
   t->stream = (cudaStream_t)o.stream;
   int dev = 0;
   cudaGetDevice(&dev);
+  t->device = dev;
   cudaDeviceGetAttribute(&t->sm_count, cudaDevAttrMultiProcessorCount, dev);
   if (t->sm_count <= 0) {
     delete t;
@@ -307,7 +365,7 @@ gt_status gt_build(const float *F, int64_t N, int32_t d, const gt_build_opts *op
   if (st == GT_OK) st = tree_build_level0(t, (const float *)Fd, 0, N, perm_dev, s);
   if (st == GT_OK) st = read_flags(t, s, hflags);
   if (st == GT_OK && hflags[kFlagDomain])
-    st = set_error(GT_EDOMAIN, "F has a negative or non-finite entry");
+    st = set_error(GT_EDOMAIN, split ? "F has a non-finite entry" : "F has a negative or non-finite entry");
   if (st == GT_OK) st = pre ? prefix_build(t, 0, N, s) : tree_build_levels(t, 0, N, s);
   if (st == GT_OK) {
     cudaError_t e = cudaStreamSynchronize(s);
@@ -339,7 +397,7 @@ gt_status gt_insert(gt_tree *t, const float *f, int64_t n_new, void *stream) {
   const void *fd = f;
   gt_status st = GT_OK;
   if (!is_device_ptr(f)) {
-    const int64_t bytes = n_new * t->d * (int64_t)sizeof(float);
+    const int64_t bytes = n_new * t->d_in * (int64_t)sizeof(float);
     st = ws_stage(t, bytes);
     if (st != GT_OK) return st;
     GT_CUDA(cudaMemcpyAsync(t->ws.stage, f, (size_t)bytes, cudaMemcpyHostToDevice, s));
@@ -350,7 +408,9 @@ gt_status gt_insert(gt_tree *t, const float *f, int64_t n_new, void *stream) {
   int hflags[kFlagCount] = {0};
   if (st == GT_OK) st = read_flags(t, s, hflags);
   if (st != GT_OK) return st;
-  if (hflags[kFlagDomain]) return set_error(GT_EDOMAIN, "inserted row has a negative or non-finite entry");
+  if (hflags[kFlagDomain])
+    return set_error(GT_EDOMAIN, t->split_sign ? "inserted row has a non-finite entry"
+                                               : "inserted row has a negative or non-finite entry");
   const int64_t first = t->N;
   t->N = N1;
   t->L = top_level(N1);
@@ -458,7 +518,7 @@ static gt_status run_search_on(gt_tree *t, const float *Q, int64_t B, const floa
       r_host = false;
     }
   }
-  const int64_t qbytes = B * t->d * (int64_t)sizeof(float);
+  const int64_t qbytes = B * t->d_in * (int64_t)sizeof(float);
   const int64_t qpad = (qbytes + 255) / 256 * 256;
   if (q_host || r_host) {
     st = ws_stage(t, qpad + B * (int64_t)sizeof(float));
@@ -504,9 +564,14 @@ static gt_status run_search_on(gt_tree *t, const float *Q, int64_t B, const floa
       return set_error(GT_EINVAL, "a prefix-layout tree's dense level is its prefix_level");
     cut = t->pc;
   } else if (exhaustive) {
+    if (t->split_sign)
+      return set_error(GT_EINVAL, "a GT_POOL_MAXMIN tree decides items by a signed recheck: "
+                                  "no exhaustive scan of its split rows");
     cut = 0;
   } else if (o.cutover >= 0) {
     if (o.cutover > t->L) return set_error(GT_EINVAL, "cutover above the root level");
+    if (o.cutover == 0 && t->split_sign)
+      return set_error(GT_EINVAL, "a GT_POOL_MAXMIN tree needs a cutover level >= 1");
     cut = o.cutover;
   } else if (o.cutover == -1) {
     // automatic: the level an earlier gt_autotune chose for this format, else
@@ -540,15 +605,18 @@ static gt_status run_search_on(gt_tree *t, const float *Q, int64_t B, const floa
   front_cap = std::min<int64_t>(front_cap, (int64_t)1 << 31);
   int64_t rchk_cap = std::max<int64_t>(1 << 14, front_cap / 16);
   int64_t res_cap = std::max<int64_t>(t->ws.res_cap, std::min<int64_t>(front_cap, B * 256));
-  st = ws_reserve_frontier(t, front_cap, res_cap, rchk_cap);
+  // the exhaustive scan's GEMM epilogue decides every item: it writes only the
+  // result and recheck lists, so its frontier buffers stay at the minimum
+  st = ws_reserve_frontier(t, exhaustive ? (1 << 10) : front_cap, res_cap, rchk_cap);
   if (st != GT_OK) return st;
   Workspace &w = t->ws;
   front_cap = std::min<int64_t>(front_cap, w.front_cap);
   w.front_lim = front_cap;
 
-  int64_t bm = o.max_batch > 0 ? o.max_batch : std::max<int64_t>(1, front_cap / 65536);
+  int64_t bm = o.max_batch > 0 ? o.max_batch
+                               : (exhaustive ? B : std::max<int64_t>(1, front_cap / 65536));
   bm = std::min(bm, B);
-  bm = std::min<int64_t>(bm, front_cap);  // the root list holds one pair per query
+  if (!exhaustive) bm = std::min<int64_t>(bm, front_cap);  // the root list holds one pair per query
   uint32_t R = 0;  // results so far
   GT_CUDA(cudaMemsetAsync(w.counters, 0, 64 * sizeof(uint32_t), s));
   // the CSR output, assembled on the device behind the last micro-batch (its
@@ -648,7 +716,8 @@ static gt_status run_search_on(gt_tree *t, const float *Q, int64_t B, const floa
     // else capture one (falling back to direct launches if capture fails)
     GraphKey key;
     std::memset(&key, 0, sizeof(key));
-    key.cut = cut; key.fmt = fmt; key.timing = tm.on ? 1 : 0; key.pad = sub ? 1 : 0;
+    key.cut = cut; key.fmt = fmt; key.timing = tm.on ? 1 : 0;
+    key.pad = (sub ? 1 : 0) | (t->expire_waits ? 2 : 0);
     key.tuned_g = t->tuned_g[fmt]; key.tuned_bn = t->tuned_bn;
     key.q0 = q0; key.b = b; key.N = t->N; key.front_lim = w.front_lim;
     key.res_cap = w.res_cap; key.rchk_cap = w.rchk_cap;
@@ -729,7 +798,7 @@ static gt_status run_search_on(gt_tree *t, const float *Q, int64_t B, const floa
     }
     GT_CUDA(cudaStreamSynchronize(s));
     const uint32_t *hc = w.hcounters;
-    if (hc[64 + kFlagDomain]) return set_error(GT_EDOMAIN, "Q has a negative or non-finite entry");
+    if (hc[64 + kFlagDomain]) return set_error(GT_EDOMAIN, "Q has a negative or non-finite entry (non-finite only for a GT_POOL_MAXMIN tree)");
     if (hc[64 + kFlagRho]) return set_error(GT_EINVAL, "rho must satisfy 0 < rho <= 1");
     if (w.hcounters[64 + kFlagTimeout]) return set_error(GT_ETIMEOUT, "a bounded device wait expired");
     if (w.hcounters[64 + kFlagStray])
@@ -865,14 +934,58 @@ gt_status gt_query_into(gt_tree *t, const float *Q, int64_t B, const float *rho,
   return GT_OK;
 }
 
-gt_status gt_exhaustive(gt_tree *t, const float *Q, int64_t B, const float *rho,
-                        const gt_query_opts *opts, gt_csr *out) {
+gt_status gt_exhaustive_tree(gt_tree *t, const float *Q, int64_t B, const float *rho,
+                             const gt_query_opts *opts, gt_csr *out) {
+  if (out) std::memset(out, 0, sizeof(*out));
   if (!dense_available()) return set_error(GT_EINVAL, "dense GEMM path not available");
   gt_query_opts o;
   std::memset(&o, 0, sizeof(o));
   if (opts) o = *opts;
   o.dtype = GT_BF16;
   return run_search(t, Q, B, rho, &o, out, true);
+}
+
+gt_status gt_exhaustive(const float *F, int64_t N, int32_t d, const float *Q, int64_t B,
+                        const float *rho, const gt_query_opts *opts, gt_csr *out) {
+  if (!out) return set_error(GT_EINVAL, "null output");
+  std::memset(out, 0, sizeof(*out));
+  if (!F) return set_error(GT_EINVAL, "null F");
+  if (N < 1 || N >= ((int64_t)1 << 31)) return set_error(GT_EINVAL, "N must be in [1, 2^31)");
+  if (d < 1 || d > 2048) return set_error(GT_EINVAL, "d must be in [1, 2048]");
+  if (!dense_available()) return set_error(GT_EINVAL, "dense GEMM path not available");
+  int dev = 0;
+  GT_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return set_error(GT_EINVAL, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_scan_mutex);
+  gt_tree *x = nullptr;
+  gt_status st = scan_context(dev, N, d, &x);
+  if (st != GT_OK) return st;
+  // the caller's rows, quantised into the context (FP32 master rows for the
+  // FP64 recheck, BF16 rows for the GEMM) on the caller's stream
+  cudaStream_t s = (opts && opts->stream) ? (cudaStream_t)opts->stream : nullptr;
+  const void *Fd = F;
+  if (!is_device_ptr(F)) {
+    if (const void *p = pinned_device_view(F)) {
+      Fd = p;  // page-locked host rows are read in place
+    } else {
+      const int64_t bytes = N * (int64_t)d * (int64_t)sizeof(float);
+      st = ws_stage(x, bytes);
+      if (st != GT_OK) return st;
+      GT_CUDA(cudaMemcpyAsync(x->ws.stage, F, (size_t)bytes, cudaMemcpyHostToDevice, s));
+      Fd = x->ws.stage;
+    }
+  }
+  GT_CUDA(cudaMemsetAsync(x->flags, 0, kFlagCount * sizeof(int), s));
+  st = tree_build_level0(x, (const float *)Fd, 0, N, nullptr, s);
+  int hflags[kFlagCount] = {0};
+  if (st == GT_OK) st = read_flags(x, s, hflags);
+  if (st != GT_OK) return st;
+  if (hflags[kFlagDomain]) return set_error(GT_EDOMAIN, "F has a negative or non-finite entry");
+  gt_query_opts o;
+  std::memset(&o, 0, sizeof(o));
+  if (opts) o = *opts;
+  o.dtype = GT_BF16;
+  return run_search(x, Q, B, rho, &o, out, true);
 }
 
 gt_status gt_dense_scores(gt_tree *t, const float *Q, int64_t B, int32_t level, float *scores,
@@ -886,7 +999,7 @@ gt_status gt_dense_scores(gt_tree *t, const float *Q, int64_t B, int32_t level, 
   gt_status st = ws_reserve_queries(t, B);
   if (st != GT_OK) return st;
   const void *Qd = Q;
-  const int64_t qbytes = B * t->d * (int64_t)sizeof(float);
+  const int64_t qbytes = B * t->d_in * (int64_t)sizeof(float);
   const int64_t qpad = (qbytes + 255) / 256 * 256;
   st = ws_stage(t, qpad + B * (int64_t)sizeof(float));
   if (st != GT_OK) return st;
@@ -903,7 +1016,7 @@ gt_status gt_dense_scores(gt_tree *t, const float *Q, int64_t B, int32_t level, 
   int hflags[kFlagCount] = {0};
   st = read_flags(t, s, hflags);
   if (st != GT_OK) return st;
-  if (hflags[kFlagDomain]) return set_error(GT_EDOMAIN, "Q has a negative or non-finite entry");
+  if (hflags[kFlagDomain]) return set_error(GT_EDOMAIN, "Q has a negative or non-finite entry (non-finite only for a GT_POOL_MAXMIN tree)");
   const int64_t rows = level_rows(t->N, level);
   float *sd = scores;
   const bool host_out = !is_device_ptr(scores);
@@ -938,7 +1051,7 @@ gt_status gt_pair_bounds(gt_tree *t, int32_t level, int32_t dtype, const float *
   // staging: queries, thresholds (unused; the preparation wants valid ones),
   // pairs and scores, each 256-byte aligned
   auto pad = [](int64_t b) { return (b + 255) / 256 * 256; };
-  const int64_t qbytes = B * t->d * (int64_t)sizeof(float);
+  const int64_t qbytes = B * t->d_in * (int64_t)sizeof(float);
   const int64_t o_rho = pad(qbytes), o_pairs = o_rho + pad(B * 4), o_out = o_pairs + pad(n * 8);
   st = ws_stage(t, o_out + pad(n * 12));
   if (st != GT_OK) return st;
@@ -965,7 +1078,7 @@ gt_status gt_pair_bounds(gt_tree *t, int32_t level, int32_t dtype, const float *
   int hflags[kFlagCount] = {0};
   st = read_flags(t, s, hflags);
   if (st != GT_OK) return st;
-  if (hflags[kFlagDomain]) return set_error(GT_EDOMAIN, "Q has a negative or non-finite entry");
+  if (hflags[kFlagDomain]) return set_error(GT_EDOMAIN, "Q has a negative or non-finite entry (non-finite only for a GT_POOL_MAXMIN tree)");
   return GT_OK;
 }
 
@@ -1140,8 +1253,14 @@ gt_status gt_read_rows(const gt_tree *t, int32_t level, int32_t dtype, int64_t f
   return GT_OK;
 }
 
+gt_status gt_set_wait_expiry(gt_tree *t, int32_t on) {
+  if (!t) return set_error(GT_EINVAL, "null tree");
+  t->expire_waits = on ? 1 : 0;
+  return GT_OK;
+}
+
 int64_t gt_size(const gt_tree *t) { return t ? t->N : 0; }
-int32_t gt_dim(const gt_tree *t) { return t ? t->d : 0; }
+int32_t gt_dim(const gt_tree *t) { return t ? t->d_in : 0; }
 int32_t gt_levels(const gt_tree *t) { return t ? t->L + 1 : 0; }
 
 void gt_free(gt_tree *t) {

@@ -142,7 +142,11 @@ struct GraphCache {
 struct gt_tree {
   int64_t N = 0;     // items
   int64_t cap = 0;   // items storable without reallocation
-  int32_t d = 0;
+  int32_t d = 0;     // entries per stored row (2 d_in for split signed rows)
+  int32_t d_in = 0;  // entries per row of the caller's inputs
+  bool split_sign = false;  // GT_POOL_MAXMIN: rows and queries stored as
+                            // [max(x, 0), max(-x, 0)], max pools over them,
+                            // items decided by a signed FP64 dot product
   int32_t L = 0;     // top level: ceil(log2 N)
   int32_t Lcap = 0;  // top level storable: ceil(log2 cap)
   int64_t stride = 0;            // entries per stored row (d rounded up to 64)
@@ -158,6 +162,7 @@ struct gt_tree {
   float max_norm_dev = 0.f;      // max | ||f||_2 - 1 | seen at build / insert
   cudaStream_t stream = nullptr;
   int sm_count = 0;
+  int device = 0;                // CUDA device the tree's memory lives on
   int tuned_cut[3] = {0, 0, 0};  // cutover level chosen by gt_autotune, per row format
   int tuned_g[3] = {0, 0, 0};    // tests in flight per warp chosen by gt_autotune
   int tuned_bn = 0;              // dense GEMM pool-tile width (0: 256)
@@ -170,6 +175,7 @@ struct gt_tree {
   float *pref32 = nullptr;
   int tuned_sub[3] = {0, 0, 0};  // gt_autotune's choice: 1 subtraction path, -1 direct, 0 untuned
   int ring_batch = 32;           // k_ring's pairs per warp batch for the current launches
+  int expire_waits = 0;          // gt_set_wait_expiry: ring kernels' first wait gives up
   bool graphs_ok = true;         // false after a failed capture: launch directly
   gt::GraphCache *graphs = nullptr;  // captured micro-batches (a pointer: views copy it)
   cudaStream_t aux_stream = nullptr; // capturable stream for legacy-stream callers

@@ -217,6 +217,7 @@ gt_status gt_server_create(gt_tree *t, const gt_server_opts *opts, gt_server **o
   if (!t || !out) return set_error(GT_EINVAL, "null argument");
   *out = nullptr;
   if (t->layout == GT_LAYOUT_PREFIX) return set_error(GT_EINVAL, "not available for a prefix-layout tree");
+  if (t->split_sign) return set_error(GT_EINVAL, "not available for a GT_POOL_MAXMIN tree");
   gt_server_opts o;
   std::memset(&o, 0, sizeof(o));
   o.dtype = GT_BF16;

@@ -15,10 +15,21 @@
 // host code its name is only a host-side stand-in, so the first call on each
 // device looks up its device address with cudaGetSymbolAddress (that device
 // current) and keeps it; that first call should come before any stream
-// capture.  All calls share the array and it keeps the last call's contents:
+// capture.  The kept address belongs to the device's current context: after
+// cudaDeviceReset the process must not call gt_query_static on that device
+// again.  All calls share the array and it keeps the last call's contents:
 // each call clears the counters it relies on, and calls that overlap on the
 // GPU (on different streams, or from different threads) race on it and must
 // not be issued.
+//
+// Fixed limits of the array: 256 queries per call, rows of at most 2048
+// entries, 262,144 neighbours per call in all (the result list is shared by
+// the call's micro-batches), 65,536 leaf pairs of one micro-batch waiting for
+// the FP64 recheck, and about 1.8M (query, pool) pairs in each of the two
+// frontier lists of one micro-batch.  A micro-batch whose frontier or recheck
+// list overflows is re-run with half the queries; a call whose results
+// exceed the result list, or one query whose frontier alone does not fit,
+// returns GT_EOVERFLOW.
 #include <mutex>
 
 #include "gt_internal.cuh"
@@ -88,6 +99,10 @@ extern "C" gt_status gt_query_static(gt_tree *t, const float *Q, int64_t B, cons
   if (!is_device_ptr(Q) || !is_device_ptr(rho) || !is_device_ptr(offsets) ||
       (ids_cap > 0 && !is_device_ptr(ids)))
     return set_error(GT_EINVAL, "gt_query_static needs device pointers for Q, rho and outputs");
+  int dev = 0;
+  GT_CUDA(cudaGetDevice(&dev));
+  if (dev != t->device)
+    return set_error(GT_EINVAL, "gt_query_static must be called with the tree's device current");
   cudaStream_t s = stream ? (cudaStream_t)stream : t->stream;
   void *base = nullptr;
   gt_status st = scratch_address(&base);
@@ -123,7 +138,7 @@ extern "C" gt_status gt_query_static(gt_tree *t, const float *Q, int64_t B, cons
   GT_CUDA(cudaMemcpyAsync(hc + 64, v.flags, 16 * sizeof(int), cudaMemcpyDeviceToHost, s));
   GT_CUDA(cudaStreamSynchronize(s));
   if (hc[64 + kFlagDomain]) return set_error(GT_EDOMAIN, "Q has a negative or non-finite entry");
-  if (hc[64 + 3]) return set_error(GT_EINVAL, "rho must satisfy 0 < rho <= 1");
+  if (hc[64 + kFlagRho]) return set_error(GT_EINVAL, "rho must satisfy 0 < rho <= 1");
 
   uint32_t R = 0;
   int64_t bm = B, q0 = 0;
@@ -145,12 +160,18 @@ extern "C" gt_status gt_query_static(gt_tree *t, const float *Q, int64_t B, cons
     if (hc[64 + kFlagStray])
       return set_error(GT_ECUDA, "internal error: a list entry names a query or row outside its buffers");
     if (hc[64 + kFlagOverflow]) {
-      // roll the result list back and retry with fewer queries
+      // the result list holds every micro-batch's neighbours: fewer queries
+      // per micro-batch cannot make the call's results fit
+      if ((int64_t)hc[kMaxLevels] > kResPairs)
+        return set_error(GT_EOVERFLOW, "the call's neighbours exceed the static result list "
+                                       "(262,144 per call): split the queries over more calls");
+      // a frontier or the recheck list: roll the result list back and retry
+      // with fewer queries
       GT_CUDA(cudaMemcpyAsync(w.counters + kMaxLevels, &R, sizeof(uint32_t), cudaMemcpyHostToDevice, s));
       GT_CUDA(cudaStreamSynchronize(s));
       if (b == 1)
-        return set_error(GT_EOVERFLOW,
-                         "one query's frontier or results exceed the 32 MiB static scratch");
+        return set_error(GT_EOVERFLOW, "one query's frontier (or its leaf pairs awaiting the FP64 "
+                                       "recheck) exceeds the static scratch's lists");
       bm = b / 2;
       continue;
     }
@@ -164,6 +185,10 @@ extern "C" gt_status gt_query_static(gt_tree *t, const float *Q, int64_t B, cons
   GT_CUDA(cudaMemsetAsync(cursor, 0, (size_t)(B + 1) * sizeof(int64_t), s));
   launch_csr_into(&v, w.res, R, nullptr, 0, B, cursor, offsets, ids, w.counters + kCsrListSlot, s);
   GT_CUDA(cudaGetLastError());
+  // the CSR passes flag (and leave out) a result naming a query outside the call
+  GT_CUDA(cudaMemcpyAsync(hc + 64, v.flags, 16 * sizeof(int), cudaMemcpyDeviceToHost, s));
   GT_CUDA(cudaStreamSynchronize(s));
+  if (hc[64 + kFlagStray])
+    return set_error(GT_ECUDA, "internal error: a result names a query outside the call");
   return GT_OK;
 }

@@ -171,6 +171,12 @@ struct LevelArgs {
   // is the dense GEMM's, bounded by g_cl * s <= exact <= g_cu * s
   uint32_t pre_h, pre_c, n_items;
   float g_cu, g_cl;
+  // split signed rows (GT_POOL_MAXMIN): a leaf's score bounds q.f from above
+  // only, so every leaf that the bound keeps goes to the signed FP64 recheck
+  int no_accept;
+  // failure-detection test (gt_set_wait_limit): the ring kernels start no
+  // copy, and their first bounded wait gives up at once
+  int expire;
 };
 
 // A list entry naming a query or a row outside its buffers can only come from
@@ -268,6 +274,41 @@ __device__ __forceinline__ int refine32(const LevelArgs &a, uint32_t j, float rh
   return s * a.bd32.cl * (1.f - 0x1p-22f) >= rho ? 1 : 2;
 }
 
+// Re-score leaf item j whose low-precision bound straddles rho, warp-wide,
+// with the query entries the warp holds: from its BF16 row first for an FP8
+// tree keeping BF16 rows (half the bytes of the FP32 row; its bound is 16
+// times tighter than FP8's), then from the FP32 master row.  0 pruned, 1
+// accepted, 2 still within the FP32 bound of rho (FP64 recheck).
+template <int FMT, int KV, bool QL1>
+__device__ __forceinline__ int leaf_rescore(const LevelArgs &a, uint32_t j, float rho,
+                                            const float *qreg, const float4 *qrow,
+                                            uint32_t &n_refine) {
+  constexpr int EPV = RowFmt<FMT>::EPV;
+  const int lane = threadIdx.x & 31;
+  if (FMT == GT_FP8 && !QL1 && a.rows16) {
+    // this lane's FP8 vector v holds entries 16v .. 16v+15, two BF16 vectors
+    // of the item's BF16 row (the row is padded to the stride, so the second
+    // of the last pair stays in it)
+    const uint4 *r16 = reinterpret_cast<const uint4 *>(a.rows16 + (size_t)j * a.qstride);
+    float s16 = 0.f;
+#pragma unroll
+    for (int k = 0; k < KV; ++k) {
+      const int v = lane + 32 * k;
+      if (v < a.nvec) {
+        s16 = vdot<GT_BF16>(r16[2 * v], &qreg[k * EPV], s16);
+        s16 = vdot<GT_BF16>(r16[2 * v + 1], &qreg[k * EPV + 8], s16);
+      }
+    }
+    s16 = warp_sum(s16);
+    ++n_refine;
+    if (s16 * a.bd16.cu < rho) return 0;
+    if (s16 * a.bd16.cl * (1.f - 0x1p-22f) >= rho) return 1;
+  }
+  // FP32 refine: the same entries of the FP32 master row
+  ++n_refine;
+  return refine32<FMT, KV, QL1>(a, j, rho, qreg, qrow);
+}
+
 // Decide one tested pair from its (all-reduced) accumulator.  Sets bit `bit`
 // of m_pass (kept / accepted) or m_rchk (FP64 recheck).  At the leaves a
 // score whose low-precision bound straddles rho is first re-scored in FP32
@@ -286,6 +327,10 @@ __device__ __forceinline__ void decide(const LevelArgs &a, float acc, uint32_t j
     m_pass |= 1u << bit;
     return;
   }
+  if (a.no_accept) {
+    m_rchk |= 1u << bit;
+    return;
+  }
   if (Lo >= rho) {
     m_pass |= 1u << bit;
     return;
@@ -294,7 +339,6 @@ __device__ __forceinline__ void decide(const LevelArgs &a, float acc, uint32_t j
     m_rchk |= 1u << bit;
     return;
   }
-  const int lane = threadIdx.x & 31;
   if (FMT == GT_FP8 && !QL1 && a.rows16 && a.defer) {
     // re-scored from the BF16 row by the pass after this kernel (its rows
     // prefetched like any other gather, not waited for here)
@@ -302,32 +346,7 @@ __device__ __forceinline__ void decide(const LevelArgs &a, float acc, uint32_t j
     ++n_refine;
     return;
   }
-  if (FMT == GT_FP8 && !QL1 && a.rows16) {
-    // BF16 refine first (half the bytes of the FP32 row; its bound is 16
-    // times tighter than FP8's): this lane's FP8 vector v holds entries
-    // 16v .. 16v+15, two BF16 vectors of the item's BF16 row (the row is
-    // padded to the stride, so the second of the last pair stays in it)
-    const uint4 *r16 = reinterpret_cast<const uint4 *>(a.rows16 + (size_t)j * a.qstride);
-    float s16 = 0.f;
-#pragma unroll
-    for (int k = 0; k < KV; ++k) {
-      const int v = lane + 32 * k;
-      if (v < a.nvec) {
-        s16 = vdot<GT_BF16>(r16[2 * v], &qreg[k * EPV], s16);
-        s16 = vdot<GT_BF16>(r16[2 * v + 1], &qreg[k * EPV + 8], s16);
-      }
-    }
-    s16 = warp_sum(s16);
-    ++n_refine;
-    if (s16 * a.bd16.cu < rho) return;
-    if (s16 * a.bd16.cl * (1.f - 0x1p-22f) >= rho) {
-      m_pass |= 1u << bit;
-      return;
-    }
-  }
-  // FP32 refine: the same entries of the FP32 master row
-  ++n_refine;
-  const int r = refine32<FMT, KV, QL1>(a, j, rho, qreg, qrow);
+  const int r = leaf_rescore<FMT, KV, QL1>(a, j, rho, qreg, qrow, n_refine);
   if (r == 1)
     m_pass |= 1u << bit;
   else if (r == 2)
@@ -701,12 +720,12 @@ __device__ __forceinline__ bool ring_test(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// wait for the phase of parity `parity` of `bar`; false after kRingWaitNs
-__device__ __forceinline__ bool ring_wait(uint32_t bar, uint32_t parity) {
+// wait for the phase of parity `parity` of `bar`; false after limit_ns
+__device__ __forceinline__ bool ring_wait(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
   if (ring_test(bar, parity)) return true;
   const uint64_t t0 = ring_now();
   while (!ring_test(bar, parity)) {
-    if (ring_now() - t0 > kRingWaitNs) return false;
+    if (ring_now() - t0 > limit_ns) return false;
   }
   return true;
 }
@@ -819,6 +838,25 @@ __global__ void __launch_bounds__(32 * kRingWarps, 1)
   float qn1 = 0.f, rho = 0.f;
   uint32_t n_refine = 0;
   bool ok = true;
+  // query q's entries into registers (this lane's share), with its bounds
+  auto load_query = [&](uint32_t q) {
+    cur_q = q;
+    const float4 *qrow = reinterpret_cast<const float4 *>(a.qf32 + (size_t)q * a.qstride);
+#pragma unroll
+    for (int kk = 0; kk < KV; ++kk) {
+      const int v = lane + 32 * kk;
+#pragma unroll
+      for (int x = 0; x < EPV / 4; ++x) {
+        const float4 y = v < a.nvec ? qrow[v * (EPV / 4) + x] : make_float4(0.f, 0.f, 0.f, 0.f);
+        qreg[kk * EPV + 4 * x + 0] = y.x;
+        qreg[kk * EPV + 4 * x + 1] = y.y;
+        qreg[kk * EPV + 4 * x + 2] = y.z;
+        qreg[kk * EPV + 4 * x + 3] = y.w;
+      }
+    }
+    qn1 = a.qn1[q];
+    rho = a.rho[q];
+  };
   SibPair e_cur, e_nxt;
   uint32_t r_cur, r_nxt;
   uint32_t b = gw;
@@ -826,9 +864,11 @@ __global__ void __launch_bounds__(32 * kRingWarps, 1)
   load_batch(b + nw, e_nxt, r_nxt);
   uint32_t len_cur = batch_len(b), len_nxt = batch_len(b + nw);
   // prime the ring: the first `depth` pairs of the warp's stream (a warp's
-  // stream holds fewer than 2^32 pairs: the list's length is a uint32)
+  // stream holds fewer than 2^32 pairs: the list's length is a uint32).
+  // With a.expire (a failure-detection test) no copy is started, so the
+  // first wait below runs out with nothing in flight.
   uint32_t t_issued = 0;  // pairs of the stream whose copy was started
-  for (uint32_t k = 0; k < depth; ++k) {
+  for (uint32_t k = 0; k < (a.expire ? 0u : depth); ++k) {
     uint32_t row;
     bool have;
     if (k < len_cur) {
@@ -854,30 +894,17 @@ __global__ void __launch_bounds__(32 * kRingWarps, 1)
     uint32_t m_c = 0;            // MODE 4: the left item is tested next
     uint32_t m_d = 0;            // FP8 leaves: re-scored by the BF16 pass
     float my_ul = 0.f, my_ur = 0.f;
+    // The per-pair loop only gathers and scores: wait for the row, dot
+    // product, refill the slot, warp sum.  The score of pair i is kept by
+    // lane i, and after the batch every lane decides its own pair (the
+    // bounds, the subtraction, the prune / accept tests); the few leaf
+    // re-scores then run warp-wide, one item at a time.
+    float my_acc = 0.f;
     for (uint32_t i = 0; i < len_cur; ++i, ++t) {
       const uint32_t q = __shfl_sync(FULL, e_cur.q, i);
-      const uint32_t rowi = __shfl_sync(FULL, r_cur, i);
-      const float Up = SUB ? __shfl_sync(FULL, e_cur.U, i) : 0.f;
-      const bool has = rowi != kNoRow;
-      if (q != cur_q) {
-        cur_q = q;
-        const float4 *qrow = reinterpret_cast<const float4 *>(a.qf32 + (size_t)q * a.qstride);
-#pragma unroll
-        for (int kk = 0; kk < KV; ++kk) {
-          const int v = lane + 32 * kk;
-#pragma unroll
-          for (int x = 0; x < EPV / 4; ++x) {
-            const float4 y = v < a.nvec ? qrow[v * (EPV / 4) + x] : make_float4(0.f, 0.f, 0.f, 0.f);
-            qreg[kk * EPV + 4 * x + 0] = y.x;
-            qreg[kk * EPV + 4 * x + 1] = y.y;
-            qreg[kk * EPV + 4 * x + 2] = y.z;
-            qreg[kk * EPV + 4 * x + 3] = y.w;
-          }
-        }
-        qn1 = a.qn1[q];
-        rho = a.rho[q];
-      }
-      const bool good = ring_wait(full0 + 8u * k, ph);
+      const bool has = __shfl_sync(FULL, r_cur, i) != kNoRow;
+      if (q != cur_q) load_query(q);
+      const bool good = ring_wait(full0 + 8u * k, ph, a.expire ? 0ull : kRingWaitNs);
       if (!__all_sync(FULL, good)) {
         ok = false;
         break;
@@ -917,31 +944,64 @@ __global__ void __launch_bounds__(32 * kRingWarps, 1)
         ph ^= 1u;
       }
       acc = warp_sum(acc);
-      if (PRE) {
-        // S(mid) of entry i, decided with the batch below by the entry's lane
-        if ((uint32_t)lane == i) my_ul = acc;
-      } else if (!SUB) {
-        decide<FMT, KV, LEAF, false>(a, acc, rowi, qn1, rho, qreg, nullptr, (int)i, m_a, m_b, m_d, n_refine);
-      } else if (MODE == 4) {
-        float Ul = Up, Ur = 0.f;
-        if (has) {
-          decide<FMT, KV, true, false>(a, acc, rowi, qn1, rho, qreg, nullptr, (int)i, m_a, m_b, m_d, n_refine);
-          sub_test<FMT>(a, acc, rowi, qn1, Up, Ul, Ur);
-        }
-        if (Ul >= rho) m_c |= 1u << i;
-      } else {
-        float Ul = Up, Ur = 0.f;
-        if (has) sub_test<FMT>(a, acc, rowi, qn1, Up, Ul, Ur);
-        if (Ul >= rho) m_a |= 1u << i;
-        if (has && Ur >= rho) m_b |= 1u << i;
-        if ((uint32_t)lane == i) {
-          my_ul = Ul;
-          my_ur = Ur;
-        }
-      }
+      if ((uint32_t)lane == i) my_acc = acc;
     }
     if (!ok) break;
+    if (!PRE) {
+      // this lane's pair: its query's bound terms, the gathered row's score
+      // and bounds
+      const bool mine = (uint32_t)lane < len_cur;
+      const bool has = mine && r_cur != kNoRow;
+      const float qn1_l = mine ? a.qn1[e_cur.q] : 0.f;
+      const float rho_l = mine ? a.rho[e_cur.q] : INFINITY;
+      float U = 0.f, Lo = 0.f;
+      if (has) test_bounds<FMT>(a, my_acc, r_cur, qn1_l, U, Lo);
+      // subtraction: the left child's exact score is the parent's minus the
+      // right child's, so Ul = U_parent - L_right (rounded up) bounds it.  The
+      // last row of a level is the one pool an insert can extend after its
+      // parent's bound was taken (a server group keeps the tree of its
+      // admission while later steps append items): its current row would
+      // bound the grown pool, not the one under the parent, so it is not
+      // subtracted.
+      float Ul = e_cur.U;
+      if (SUB && has) Ul = __fsub_ru(e_cur.U, r_cur + 1u >= a.n_rows ? 0.f : fmaxf(Lo, 0.f));
+      if (MODE == 0) {
+        m_a = __ballot_sync(FULL, has && U >= rho_l);
+      } else if (MODE == 2 || MODE == 3) {
+        m_a = __ballot_sync(FULL, mine && Ul >= rho_l);
+        m_b = __ballot_sync(FULL, has && U >= rho_l);
+        my_ul = Ul;
+        my_ur = U;
+      } else {
+        // the gathered item: 0 pruned, 1 accepted, 2 FP64 recheck, 3 re-score
+        // here, 4 re-scored from its BF16 row by the pass after this kernel
+        int c = 0;
+        if (has && U >= rho_l) {
+          if (a.no_accept) c = 2;
+          else if (Lo >= rho_l) c = 1;
+          else if (FMT == GT_F32) c = 2;
+          else if (FMT == GT_FP8 && a.rows16 && a.defer) c = 4;
+          else c = 3;
+        }
+        if (MODE == 4) m_c = __ballot_sync(FULL, mine && Ul >= rho_l);
+        uint32_t need = __ballot_sync(FULL, c == 3);
+        while (need) {
+          const int j = __ffs(need) - 1;
+          need &= need - 1u;
+          const uint32_t qj = __shfl_sync(FULL, e_cur.q, j);
+          if (qj != cur_q) load_query(qj);
+          const int r = leaf_rescore<FMT, KV, false>(a, __shfl_sync(FULL, r_cur, j), rho, qreg,
+                                                     nullptr, n_refine);
+          if (lane == j) c = r;
+        }
+        m_a = __ballot_sync(FULL, c == 1);
+        m_b = __ballot_sync(FULL, c == 2);
+        m_d = __ballot_sync(FULL, c == 4);
+        n_refine += (uint32_t)__popc(m_d);
+      }
+    }
     if (PRE) {
+      my_ul = my_acc;
       // Each lane decides its own entry: the pool [lo, hi) and its prefix
       // scores S(lo), S(hi) (0 at a block's start; the GEMM's block total at
       // its end; else gathered prefix scores) and S(mid) from this batch's
@@ -991,24 +1051,7 @@ __global__ void __launch_bounds__(32 * kRingWarps, 1)
             const int j = __ffs(need) - 1;
             need &= need - 1u;
             const uint32_t qj = __shfl_sync(FULL, e_cur.q, j);
-            if (qj != cur_q) {
-              cur_q = qj;
-              const float4 *qrow = reinterpret_cast<const float4 *>(a.qf32 + (size_t)qj * a.qstride);
-#pragma unroll
-              for (int kk = 0; kk < KV; ++kk) {
-                const int v = lane + 32 * kk;
-#pragma unroll
-                for (int x = 0; x < EPV / 4; ++x) {
-                  const float4 y = v < a.nvec ? qrow[v * (EPV / 4) + x] : make_float4(0.f, 0.f, 0.f, 0.f);
-                  qreg[kk * EPV + 4 * x + 0] = y.x;
-                  qreg[kk * EPV + 4 * x + 1] = y.y;
-                  qreg[kk * EPV + 4 * x + 2] = y.z;
-                  qreg[kk * EPV + 4 * x + 3] = y.w;
-                }
-              }
-              qn1 = a.qn1[qj];
-              rho = a.rho[qj];
-            }
+            if (qj != cur_q) load_query(qj);
             const uint32_t pos = (__shfl_sync(FULL, e_cur.p, j) << a.pre_h) + side;
             ++n_refine;
             const int r = refine32<FMT, KV, false>(a, pos, rho, qreg, nullptr);
@@ -1139,10 +1182,14 @@ __global__ void __launch_bounds__(256) k_pair_bounds(const LevelArgs a, const in
 // q.f >= rho from the FP32 rows (products of FP32 values are exact in FP64).
 // Few pairs reach it, so each warp takes one pair at a time (grid-strided)
 // and the FP64 dot products of different pairs run in parallel.
+//
+// Split signed rows (d_half > 0): the stored item and query rows are
+// [max(x, 0), max(-x, 0)], so x_j = row_j - row_{d_half + j} exactly, and the
+// recheck forms the signed q.f from those differences (exact FP64 products).
 __global__ void __launch_bounds__(256) k_recheck(const Pair *__restrict__ rchk,
                                                  const uint32_t *count, uint32_t cap,
                                                  const float *__restrict__ rows32,
-                                                 int64_t stride, int nv4,
+                                                 int64_t stride, int nv4, int d_half,
                                                  const float *__restrict__ qf32,
                                                  const float *__restrict__ rho, Pair *res,
                                                  uint32_t *res_count, uint32_t res_cap,
@@ -1157,15 +1204,25 @@ __global__ void __launch_bounds__(256) k_recheck(const Pair *__restrict__ rchk,
       if (lane == 0) atomicExch(&flags[kFlagStray], 1);
       continue;
     }
-    const float4 *f = reinterpret_cast<const float4 *>(rows32 + (size_t)pr.j * stride);
-    const float4 *qq = reinterpret_cast<const float4 *>(qf32 + (size_t)pr.q * stride);
     double acc = 0.0;
-    for (int v = lane; v < nv4; v += 32) {
-      const float4 x = f[v], y = qq[v];
-      acc = fma((double)x.x, (double)y.x, acc);
-      acc = fma((double)x.y, (double)y.y, acc);
-      acc = fma((double)x.z, (double)y.z, acc);
-      acc = fma((double)x.w, (double)y.w, acc);
+    if (d_half > 0) {
+      const float *f = rows32 + (size_t)pr.j * stride;
+      const float *qq = qf32 + (size_t)pr.q * stride;
+      for (int j = lane; j < d_half; j += 32) {
+        const double x = (double)f[j] - (double)f[d_half + j];
+        const double y = (double)qq[j] - (double)qq[d_half + j];
+        acc = fma(x, y, acc);
+      }
+    } else {
+      const float4 *f = reinterpret_cast<const float4 *>(rows32 + (size_t)pr.j * stride);
+      const float4 *qq = reinterpret_cast<const float4 *>(qf32 + (size_t)pr.q * stride);
+      for (int v = lane; v < nv4; v += 32) {
+        const float4 x = f[v], y = qq[v];
+        acc = fma((double)x.x, (double)y.x, acc);
+        acc = fma((double)x.y, (double)y.y, acc);
+        acc = fma((double)x.z, (double)y.z, acc);
+        acc = fma((double)x.w, (double)y.w, acc);
+      }
     }
     acc = warp_sum_d(acc);
     if (lane == 0 && acc >= (double)rho[pr.q]) {
@@ -1179,9 +1236,12 @@ __global__ void __launch_bounds__(256) k_recheck(const Pair *__restrict__ rchk,
 }
 
 // Queries: pad to the row stride (FP32 and BF16), |q|_1 upper bound, domain
-// checks on entries and thresholds.  One warp per query.
+// checks on entries and thresholds.  One warp per query.  With `split`
+// (signed rows) a query of d entries is stored as [max(q, 0), max(-q, 0)],
+// and only non-finite entries are refused.
 __global__ void __launch_bounds__(256) k_prep_queries(const float *__restrict__ Q, int64_t B, int d,
-                                                      int64_t stride, const float *__restrict__ rho_in,
+                                                      int split, int64_t stride,
+                                                      const float *__restrict__ rho_in,
                                                       float *qf32, __nv_bfloat16 *qbf16, float *qn1,
                                                       float *rho_out, int *flags) {
   const int lane = threadIdx.x & 31;
@@ -1192,8 +1252,17 @@ __global__ void __launch_bounds__(256) k_prep_queries(const float *__restrict__ 
     float s = 0.f;
     bool bad = false;
     for (int64_t j = lane; j < stride; j += 32) {
-      float x = j < d ? in[j] : 0.f;
-      bad |= !(x >= 0.f) || !isfinite(x);
+      float x;
+      if (!split) {
+        x = j < d ? in[j] : 0.f;
+        bad |= !(x >= 0.f) || !isfinite(x);
+      } else if (j < 2 * (int64_t)d) {
+        const float y = in[j < d ? j : j - d];
+        bad |= !isfinite(y);
+        x = j < d ? (y > 0.f ? y : 0.f) : (y < 0.f ? -y : 0.f);
+      } else {
+        x = 0.f;
+      }
       s += x;
       qf32[q * stride + j] = x;
       if (qbf16) qbf16[q * stride + j] = __float2bfloat16_rn(x);
@@ -1201,8 +1270,9 @@ __global__ void __launch_bounds__(256) k_prep_queries(const float *__restrict__ 
     s = warp_sum(s);
     if (__any_sync(FULL, bad) && lane == 0) atomicExch(&flags[kFlagDomain], 1);
     if (lane == 0) {
-      // fl32 sum of d non-negative terms: exact |q|_1 <= s / (1 - gamma_d)
-      qn1[q] = s * (1.f + 2.f * (float)(d + 1) * 0x1p-24f);
+      // fl32 sum of n non-negative terms: exact |q|_1 <= s / (1 - gamma_n)
+      const int n_terms = split ? 2 * d : d;
+      qn1[q] = s * (1.f + 2.f * (float)(n_terms + 1) * 0x1p-24f);
       const float r = rho_in[q];
       if (!(r > 0.f) || !(r <= 1.f)) atomicExch(&flags[kFlagRho], 1);
       rho_out[q] = r;
@@ -1693,8 +1763,8 @@ void launch_prep_queries(gt_tree *t, const float *Q_dev, const float *rho_dev, i
   Workspace &w = t->ws;
   int blocks = (int)std::min<int64_t>((B + 7) / 8, (int64_t)t->sm_count * 8);
   if (blocks < 1) blocks = 1;
-  k_prep_queries<<<blocks, 256, 0, s>>>(Q_dev, B, t->d, t->stride, rho_dev, w.qf32, w.qbf16,
-                                        w.qn1, w.rho, t->flags);
+  k_prep_queries<<<blocks, 256, 0, s>>>(Q_dev, B, t->d_in, t->split_sign ? 1 : 0, t->stride,
+                                        rho_dev, w.qf32, w.qbf16, w.qn1, w.rho, t->flags);
 }
 
 void launch_root(gt_tree *t, int64_t q0, int64_t b, Pair *out, uint32_t *count, cudaStream_t s) {
@@ -1728,6 +1798,7 @@ bool launch_prefix(gt_tree *t, int fmt, int h, const SibPair *in, const uint32_t
   Workspace &w = t->ws;
   LevelArgs a;
   std::memset(&a, 0, sizeof(a));
+  a.expire = t->expire_waits;
   const int eb = entry_bytes(fmt);
   a.rows = fmt == GT_F32 ? reinterpret_cast<const uint8_t *>(t->pref32)
                          : reinterpret_cast<const uint8_t *>(t->pref16);
@@ -1784,7 +1855,8 @@ bool launch_prefix(gt_tree *t, int fmt, int h, const SibPair *in, const uint32_t
 }
 
 bool defer_active(const gt_tree *t, int fmt) {
-  return fmt == GT_FP8 && t->ws.defer && t->rows16;
+  // split signed rows accept no leaf on a bound: nothing is deferred
+  return fmt == GT_FP8 && t->ws.defer && t->rows16 && !t->split_sign;
 }
 
 // The deferred FP8 leaf pairs, re-scored from the BF16 item rows by the
@@ -1794,6 +1866,7 @@ static void launch_deferred_bf16(gt_tree *t, cudaStream_t s) {
   Workspace &w = t->ws;
   LevelArgs a;
   std::memset(&a, 0, sizeof(a));
+  a.expire = t->expire_waits;
   a.rows = reinterpret_cast<const uint8_t *>(t->rows16);  // level 0 starts at row 0
   a.row_bytes = t->stride * 2;
   a.nvec = (int)((t->d * 2 + 15) / 16);
@@ -1827,6 +1900,7 @@ void launch_level(gt_tree *t, int fmt, int h, int64_t /*q0*/, const Pair *in,
   Workspace &w = t->ws;
   LevelArgs a;
   std::memset(&a, 0, sizeof(a));
+  a.expire = t->expire_waits;
   const int eb = entry_bytes(fmt);
   const uint8_t *base = fmt == GT_F32 ? reinterpret_cast<const uint8_t *>(t->rows32)
                         : fmt == GT_BF16 ? reinterpret_cast<const uint8_t *>(t->rows16)
@@ -1869,6 +1943,7 @@ void launch_level(gt_tree *t, int fmt, int h, int64_t /*q0*/, const Pair *in,
     else if (fmt == GT_BF16) launch_level_f<GT_BF16, false>(a, d, t->sm_count, s);
     else launch_level_f<GT_FP8, false>(a, d, t->sm_count, s);
   } else {
+    a.no_accept = t->split_sign ? 1 : 0;
     const bool defer = defer_active(t, fmt);
     if (defer) {
       cudaMemsetAsync(w.counters + kDeferSlot, 0, sizeof(uint32_t), s);
@@ -1888,6 +1963,7 @@ void launch_pair_bounds(gt_tree *t, int fmt, int h, const int32_t *pairs, int64_
   Workspace &w = t->ws;
   LevelArgs a;
   std::memset(&a, 0, sizeof(a));
+  a.expire = t->expire_waits;
   const int eb = entry_bytes(fmt);
   const uint8_t *base = fmt == GT_F32 ? reinterpret_cast<const uint8_t *>(t->rows32)
                         : fmt == GT_BF16 ? reinterpret_cast<const uint8_t *>(t->rows16)
@@ -1919,6 +1995,7 @@ void launch_level_sub(gt_tree *t, int fmt, int h, const SibPair *in, const uint3
   Workspace &w = t->ws;
   LevelArgs a;
   std::memset(&a, 0, sizeof(a));
+  a.expire = t->expire_waits;
   const int eb = entry_bytes(fmt);
   const uint8_t *base = fmt == GT_F32 ? reinterpret_cast<const uint8_t *>(t->rows32)
                         : fmt == GT_BF16 ? reinterpret_cast<const uint8_t *>(t->rows16)
@@ -1985,6 +2062,7 @@ void launch_items_sub(gt_tree *t, int fmt, const SibPair *in, const uint32_t *in
   Workspace &w = t->ws;
   LevelArgs a;
   std::memset(&a, 0, sizeof(a));
+  a.expire = t->expire_waits;
   const int eb = entry_bytes(fmt);
   const uint8_t *base = fmt == GT_F32 ? reinterpret_cast<const uint8_t *>(t->rows32)
                         : fmt == GT_BF16 ? reinterpret_cast<const uint8_t *>(t->rows16)
@@ -2048,7 +2126,8 @@ void launch_recheck(gt_tree *t, int64_t /*q0*/, cudaStream_t s) {
   static int per_sm = 0;
   const int grid = grid_for((const void *)k_recheck, 256, t->sm_count, per_sm);
   k_recheck<<<grid, 256, 0, s>>>(w.rchk, w.counters + kMaxLevels + 1, (uint32_t)w.rchk_cap,
-                                 t->rows32, t->stride, (int)((t->d + 3) / 4), w.qf32, w.rho, w.res,
+                                 t->rows32, t->stride, (int)((t->d + 3) / 4),
+                                 t->split_sign ? t->d_in : 0, w.qf32, w.rho, w.res,
                                  w.counters + kMaxLevels, (uint32_t)w.res_cap, (uint32_t)w.q_cap,
                                  (uint32_t)t->N, t->flags);
 }

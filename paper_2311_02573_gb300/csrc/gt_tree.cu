@@ -84,11 +84,28 @@ __device__ __forceinline__ void write_row(const RowsOut &o, int64_t row, const f
   }
 }
 
+// Entry j of a stored row built from input row `in` (d entries): the input
+// entry itself, or with `split` (signed rows) entry j of [max(f, 0), max(-f, 0)]
+// (2d entries); zero past the row.  `bad` records a non-finite input entry
+// or, without split, a negative one.
+__device__ __forceinline__ float row_entry(const float *in, int d, bool split, int j, bool &bad) {
+  if (!split) {
+    const float x = j < d ? __ldg(in + j) : 0.f;
+    bad |= !(x >= 0.f) || !isfinite(x);
+    return x;
+  }
+  if (j >= 2 * d) return 0.f;
+  const float x = __ldg(in + (j < d ? j : j - d));
+  bad |= !isfinite(x);
+  return j < d ? (x > 0.f ? x : 0.f) : (x < 0.f ? -x : 0.f);
+}
+
 // Level 0: gather input rows (d contiguous floats each, any alignment), check
-// the domain, pad to the row stride with zeros.
+// the domain, pad to the row stride with zeros (signed rows: split first).
 template <int KV4>
 __global__ void __launch_bounds__(256) k_level0(const float *__restrict__ F, int64_t first,
-                                                int64_t n, int d, const int32_t *__restrict__ perm,
+                                                int64_t n, int d, int split,
+                                                const int32_t *__restrict__ perm,
                                                 int32_t *__restrict__ perm_out, RowsOut o,
                                                 int *flags, unsigned *norm_dev_bits) {
   const int lane = threadIdx.x & 31;
@@ -112,8 +129,7 @@ __global__ void __launch_bounds__(256) k_level0(const float *__restrict__ F, int
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         int j = 4 * i + c;
-        x[c] = (i < nv4 && j < d) ? __ldg(in + j) : 0.f;
-        bad |= !(x[c] >= 0.f) || !isfinite(x[c]);
+        x[c] = i < nv4 ? row_entry(in, d, split != 0, j, bad) : 0.f;
         ss = fmaf(x[c], x[c], ss);
       }
       v[k] = make_float4(x[0], x[1], x[2], x[3]);
@@ -328,7 +344,8 @@ gt_status tree_build_level0(gt_tree *t, const float *F_dev, int64_t first, int64
   const int kv = kv4_for(t->stride);
   unsigned *nb = reinterpret_cast<unsigned *>(t->flags + 32);
   int blocks = (int)std::min<int64_t>((n + 7) / 8, (int64_t)t->sm_count * 8);
-  GT_DISPATCH_KV4(kv, k_level0<KV><<<blocks, 256, 0, s>>>(F_dev, first, n, t->d, perm_dev,
+  GT_DISPATCH_KV4(kv, k_level0<KV><<<blocks, 256, 0, s>>>(F_dev, first, n, t->d_in,
+                                                          t->split_sign ? 1 : 0, perm_dev,
                                                           t->perm, o, t->flags, nb));
   GT_CUDA(cudaGetLastError());
   return GT_OK;

@@ -15,7 +15,7 @@ from . import build as _build
 
 GT_F32, GT_BF16, GT_FP8 = 0, 1, 2
 DTYPES = {"f32": GT_F32, "bf16": GT_BF16, "fp8": GT_FP8}
-POOLING = {"sum": 0, "max": 1}
+POOLING = {"sum": 0, "max": 1, "maxmin": 2}
 LAYOUTS = {"tree": 0, "prefix": 1}
 STATUS = {0: "GT_OK", 1: "GT_EINVAL", 2: "GT_EDOMAIN", 3: "GT_ENOMEM", 4: "GT_ECUDA",
           5: "GT_ETIMEOUT", 6: "GT_EOVERFLOW", 7: "GT_EBUSY"}
@@ -90,10 +90,11 @@ class GTError(RuntimeError):
 
 
 _lib = None
-ENTRY_POINTS = ("gt_build", "gt_insert", "gt_query", "gt_query_into", "gt_exhaustive", "gt_read_rows",
+ENTRY_POINTS = ("gt_build", "gt_insert", "gt_query", "gt_query_into", "gt_exhaustive",
+                "gt_exhaustive_tree", "gt_read_rows",
                 "gt_dense_scores", "gt_pair_bounds", "gt_query_static", "gt_server_create", "gt_server_submit",
                 "gt_server_insert", "gt_server_step", "gt_server_poll", "gt_server_get_stats",
-                "gt_server_free", "gt_autotune", "gt_set_tuning",
+                "gt_server_free", "gt_autotune", "gt_set_tuning", "gt_set_wait_expiry",
                 "gt_size", "gt_dim", "gt_levels", "gt_free", "gt_csr_free", "gt_last_error")
 
 
@@ -115,7 +116,9 @@ def load(build_if_missing: bool = True):
     lib.gt_build.argtypes = [P, _c_i64, _c_i32, ctypes.POINTER(BuildOpts), ctypes.POINTER(P)]
     lib.gt_insert.argtypes = [P, P, _c_i64, P]
     lib.gt_query.argtypes = [P, P, _c_i64, P, ctypes.POINTER(QueryOpts), ctypes.POINTER(CSR)]
-    lib.gt_exhaustive.argtypes = lib.gt_query.argtypes
+    lib.gt_exhaustive_tree.argtypes = lib.gt_query.argtypes
+    lib.gt_exhaustive.argtypes = [P, _c_i64, _c_i32, P, _c_i64, P, ctypes.POINTER(QueryOpts),
+                                  ctypes.POINTER(CSR)]
     lib.gt_query_into.argtypes = [P, P, _c_i64, P, ctypes.POINTER(QueryOpts), P, P, _c_i64,
                                   ctypes.POINTER(_c_i64)]
     lib.gt_query_into.restype = _c_i32
@@ -138,9 +141,12 @@ def load(build_if_missing: bool = True):
     lib.gt_autotune.restype = _c_i32
     lib.gt_set_tuning.argtypes = [P, _c_i32, _c_i32, _c_i32, _c_i32]
     lib.gt_set_tuning.restype = _c_i32
+    lib.gt_set_wait_expiry.argtypes = [P, _c_i32]
+    lib.gt_set_wait_expiry.restype = _c_i32
     lib.gt_server_free.argtypes = [P]
     lib.gt_server_free.restype = None
-    for f in ("gt_build", "gt_insert", "gt_query", "gt_exhaustive", "gt_read_rows",
+    for f in ("gt_build", "gt_insert", "gt_query", "gt_exhaustive", "gt_exhaustive_tree",
+              "gt_read_rows",
               "gt_dense_scores", "gt_pair_bounds"):
         getattr(lib, f).restype = _c_i32
     lib.gt_size.argtypes = [P]
@@ -193,6 +199,45 @@ def _out_ptr(x, dtype):
     if not isinstance(x, np.ndarray) or x.dtype != dtype or not x.flags.c_contiguous:
         raise TypeError(f"output buffer must be a C-contiguous {np.dtype(dtype)} array")
     return ctypes.c_void_p(x.ctypes.data)
+
+
+def _static_arg(x, name: str, dtype: str, ndim: int = 1) -> int:
+    """Check an argument of gt_query_static (a contiguous torch tensor of
+    `dtype` with `ndim` dimensions) and return its length along dim 0."""
+    if not hasattr(x, "data_ptr") or not hasattr(x, "is_cuda"):
+        raise TypeError(f"{name} must be a torch tensor")
+    if str(x.dtype) != f"torch.{dtype}":
+        raise TypeError(f"{name} must be {dtype}, got {x.dtype}")
+    if x.dim() != ndim:
+        raise ValueError(f"{name} must have {ndim} dimension(s), got {x.dim()}")
+    if not x.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return int(x.shape[0])
+
+
+def exhaustive(F, Q, rho, max_batch: int = 0, scratch_bytes: int = 0,
+               results_on_device: bool = False, stream=None, timing: bool = False) -> Result:
+    """gt_exhaustive: {i : q.f_i >= rho} over the rows of F (N x d) for every
+    query, by a dense scan of every (query, item) pair (no tree)."""
+    lib = load()
+    keep = []
+    N, d = _rows(F)
+    B = int(Q.shape[0])
+    st = QueryStats()
+    o = QueryOpts()
+    o.stream = _stream_ptr(stream)
+    o.dtype = GT_BF16
+    o.max_batch = max_batch
+    o.scratch_bytes = scratch_bytes
+    o.results_on_device = 1 if results_on_device else 0
+    o.timing = 1 if timing else 0
+    o.stats = ctypes.pointer(st)
+    if np.isscalar(rho):
+        rho = np.full(B, rho, dtype=np.float32)
+    csr = CSR()
+    _check(lib.gt_exhaustive(_ptr(F, keep), N, d, _ptr(Q, keep), B, _ptr(rho, keep),
+                             ctypes.byref(o), ctypes.byref(csr)))
+    return Result(csr, st)
 
 
 def _stream_ptr(stream):
@@ -261,6 +306,8 @@ class Tree:
         o.prefix_level = prefix_level
         self.layout = o.layout
         self.prefix_level = (prefix_level or 3) if o.layout == 1 else 0
+        # stored rows: 2d entries ([max(f, 0), max(-f, 0)]) for signed descriptors
+        self.row_width = 2 * d if o.pooling == POOLING["maxmin"] else d
         h = _c_p()
         _check(lib.gt_build(_ptr(F, keep), N, d, ctypes.byref(o), ctypes.byref(h)))
         self._h = h
@@ -338,20 +385,35 @@ class Tree:
 
     def exhaustive(self, Q, rho, max_batch: int = 0, scratch_bytes: int = 0,
                    results_on_device: bool = False, stream=None, timing: bool = False) -> Result:
-        """gt_exhaustive: the same sets by a dense scan of every item."""
-        return self._search(load().gt_exhaustive, Q, rho, "bf16", 0, max_batch, scratch_bytes,
-                            results_on_device, stream, timing)
+        """gt_exhaustive_tree: the same sets by a dense scan of the tree's items."""
+        return self._search(load().gt_exhaustive_tree, Q, rho, "bf16", 0, max_batch,
+                            scratch_bytes, results_on_device, stream, timing)
 
     def query_static(self, Q, rho, offsets, ids, dtype="bf16", stream=None) -> int:
-        """gt_query_static: the allocation-free query.  Q, rho, offsets (B+1
-        int64) and ids (int32) are CUDA tensors the caller owns; returns the
-        number of neighbours written."""
+        """gt_query_static: the allocation-free query.  Q (B x d float32),
+        rho (B float32), offsets (B+1 int64) and ids (int32) are contiguous
+        CUDA tensors the caller owns; returns the number of neighbours
+        written.  Arguments of the wrong type, shape or device are refused
+        here, before the library is called (it reads and writes them in
+        place, so a short or mistyped buffer would be accessed out of
+        bounds)."""
+        B = _static_arg(Q, "Q", "float32", ndim=2)
+        if B < 1 or int(Q.shape[1]) != self.dim:
+            raise ValueError(f"Q must have shape (B >= 1, {self.dim}), got {tuple(Q.shape)}")
+        if _static_arg(rho, "rho", "float32") < B:
+            raise ValueError(f"rho holds fewer than B = {B} thresholds")
+        if _static_arg(offsets, "offsets", "int64") < B + 1:
+            raise ValueError(f"offsets holds fewer than B + 1 = {B + 1} entries")
+        n_ids = _static_arg(ids, "ids", "int32")
+        for x in (Q, rho, offsets, ids):
+            if not x.is_cuda:
+                raise TypeError("gt_query_static takes CUDA tensors only")
         n = _c_i64(0)
         st = load().gt_query_static(
-            self._h, ctypes.c_void_p(Q.data_ptr()), int(Q.shape[0]),
+            self._h, ctypes.c_void_p(Q.data_ptr()), B,
             ctypes.c_void_p(rho.data_ptr()), DTYPES[dtype] if isinstance(dtype, str) else dtype,
-            ctypes.c_void_p(offsets.data_ptr()), ctypes.c_void_p(ids.data_ptr()),
-            int(ids.numel()), ctypes.byref(n), _stream_ptr(stream))
+            _out_ptr(offsets, np.int64), _out_ptr(ids, np.int32),
+            n_ids, ctypes.byref(n), _stream_ptr(stream))
         if st != 0:
             err = GTError(st, load().gt_last_error().decode())
             err.n_results = n.value
@@ -383,6 +445,11 @@ class Tree:
         _check(load().gt_set_tuning(self._h, DTYPES[dtype] if isinstance(dtype, str) else dtype,
                                     cutover, inflight, tile))
 
+    def set_wait_expiry(self, on: bool):
+        """gt_set_wait_expiry: make the gather kernels' first bounded wait run
+        out at once (the timeout path, for tests)."""
+        _check(load().gt_set_wait_expiry(self._h, 1 if on else 0))
+
     def dense_scores(self, Q, level: int, stream=None) -> np.ndarray:
         """gt_dense_scores: raw tensor-core scores (B x rows of `level`)."""
         keep = []
@@ -408,7 +475,7 @@ class Tree:
 
     def read_rows(self, level: int, dtype="f32", first: int = 0, count: int | None = None):
         fmt = DTYPES[dtype]
-        N, d = self.size, self.dim
+        N, d = self.size, self.row_width
         # level -1: a prefix-layout tree's prefix rows (one per item)
         rows = N if level < 0 else (N + (1 << level) - 1) >> level
         count = rows - first if count is None else count

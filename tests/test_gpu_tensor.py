@@ -128,6 +128,61 @@ def test_exhaustive_parity_and_rechecks(gt, small_ds):
     t2.close()
 
 
+def test_exhaustive_over_raw_database(gt, small_ds):
+    """gt_exhaustive(F, N, d, Q, B, rho): the Exh comparator (Sec. 4) over the
+    caller's rows, no tree: equal to the FP64 definition element by element."""
+    ds = small_ds
+    r = ds.rho_for(0.9)
+    ref = oracle.brute_force(ds.F, ds.Q, r)
+    assert ref.ambiguous.sum() == 0
+    N, B = ds.F.shape[0], ds.Q.shape[0]
+    Fd = torch.from_numpy(ds.F).cuda()
+    Fp = torch.from_numpy(ds.F).pin_memory()
+    # pageable host rows, device rows, page-locked host rows; device queries
+    for F, Q in ((ds.F, ds.Q), (Fd, ds.Q), (Fp, torch.from_numpy(ds.Q).cuda()), (ds.F, ds.Q)):
+        res = gt.exhaustive(F, Q, r)
+        same_sets(res, ref)
+        assert res.stats["dense_tests"] == N * B and res.stats["gathered_tests"] == 0
+    res = gt.exhaustive(Fd, ds.Q, r, results_on_device=True, max_batch=37)
+    assert res.on_device and res.stats["micro_batches"] == 3
+    res.free()
+    # a smaller database after a larger one (storage kept), then another width
+    sub = np.ascontiguousarray(ds.F[:777])
+    same_sets(gt.exhaustive(sub, ds.Q, r), oracle.brute_force(sub, ds.Q, r))
+    small = synth.generate(synth.Workload("t", 3000, 64, 129, (0.9,), "uniform:5", seed=64),
+                           screen=True)
+    r64 = small.rho_for(0.9)
+    same_sets(gt.exhaustive(small.F, small.Q, r64), oracle.brute_force(small.F, small.Q, r64))
+    # rho given per query, one threshold differing
+    r2 = r.copy()
+    r2[::2] = np.float32(0.95)
+    ref2 = oracle.brute_force(ds.F, ds.Q, r2)
+    if ref2.ambiguous.sum() == 0:
+        same_sets(gt.exhaustive(ds.F, ds.Q, r2), ref2)
+    # a negative entry in F is refused, and the context still works afterwards
+    bad = ds.F[:100].copy()
+    bad[7, 3] = -1e-3
+    with pytest.raises(gt.GTError) as e:
+        gt.exhaustive(bad, ds.Q, r)
+    assert e.value.status == 2
+    same_sets(gt.exhaustive(ds.F, ds.Q, r), ref)
+
+
+def test_exhaustive_raw_near_threshold_rechecks(gt):
+    # items within 2e-5 of rho: every one settled by the FP64 recheck
+    rho = np.float32(0.8)
+    x = np.array([rho + 2e-5, rho - 2e-5] * 40 + [0.1] * 100, dtype=np.float32)
+    d = 16
+    F = np.zeros((x.size, d), np.float32)
+    F[:, 0] = x
+    F[:, 1] = np.sqrt(1 - x.astype(np.float64) ** 2).astype(np.float32)
+    q = np.zeros((1, d), np.float32)
+    q[0, 0] = 1.0
+    res = gt.exhaustive(F, q, rho)
+    same_sets(res, oracle.brute_force(F, q, rho))
+    assert res.stats["rechecks"] >= 80 and res.stats["results"] == 40
+
+
 def test_cutover_with_micro_batches(gt, small_ds):
     ds = small_ds
     r = ds.rho_for(0.9)
