@@ -223,7 +223,8 @@ def _dist():
     return ws, rank, local
 
 
-def serve_run(gt, tree, Q, rhos, rate, n_req, dtype, inserts=None, insert_frac=0.01, seed=0):
+def serve_run(gt, tree, Q, rhos, rate, n_req, dtype, inserts=None, insert_frac=0.01, seed=0,
+              schedule="auto"):
     """Poisson request stream through the continuous-batching server.
 
     Returns achieved queries/s (completed / span from first arrival to last
@@ -238,7 +239,7 @@ def serve_run(gt, tree, Q, rhos, rate, n_req, dtype, inserts=None, insert_frac=0
     Qreq = np.ascontiguousarray(Q[qi])   # the requests' vectors, made before the clock starts
     rho = rhos[rng.integers(0, len(rhos), n_req)].astype(np.float32)
     is_ins = rng.random(n_req) < insert_frac if inserts is not None else np.zeros(n_req, bool)
-    srv = gt.Server(tree, dtype=dtype, queue_capacity=n_req)
+    srv = gt.Server(tree, dtype=dtype, queue_capacity=n_req, schedule=schedule)
     lat = np.full(n_req, np.nan)
     sub = 0
     n_done = 0
@@ -278,7 +279,8 @@ def serve_run(gt, tree, Q, rhos, rate, n_req, dtype, inserts=None, insert_frac=0
             "p50_ms": round(float(np.percentile(l, 50)), 3),
             "p99_ms": round(float(np.percentile(l, 99)), 3),
             "steps": st["steps"], "mean_group": round(st["admitted"] / max(1, st["steps"]), 1),
-            "cutover": st["cutover"], "launches": st["launches"]}
+            "cutover": st["cutover"], "launches": st["launches"],
+            "schedule": {1: "levels", 2: "drain"}.get(st["schedule"], st["schedule"])}
 
 
 
@@ -462,9 +464,9 @@ def main():
     _note("building the tree")
     pre = a.layout == "prefix"
     if pre:
-        # no autotuner, server or comparators for this layout: its GEMM level is
-        # fixed by the build, and the other legs run the tree
-        a.no_comparators = a.no_serve = a.no_stream = True
+        # no comparators or streaming run for this layout (they run the tree);
+        # its GEMM level is fixed by the build, the autotuner picks the tile
+        a.no_comparators = a.no_stream = True
         tree = gt.Tree(Fd, capacity=N + 65536, layout="prefix", prefix_level=a.prefix_level,
                        formats=("bf16", "f32") if a.dtype == "f32" else None)
     else:
@@ -481,7 +483,7 @@ def main():
         tree.set_tuning(a.dtype, tile=a.tile)
     if a.inflight and not pre:
         tree.set_tuning(a.dtype, inflight=a.inflight)
-    if a.cutover == -1 and not pre:
+    if a.cutover == -1:
         # the autotuner picks the cutover level and tests in flight per warp on
         # a sample batch (setup, outside the timed region)
         ns = a.tune_sample or B
@@ -648,7 +650,7 @@ def main():
         N_, stride_ = ds.F.shape[0], (ds.F.shape[1] + 63) // 64 * 64
         rows_tree = sum((N_ + (1 << h) - 1) >> h for h in range(0, 64) if (1 << h) < 2 * N_)
         ptree = gt.Tree(torch.from_numpy(ds.F).to(dev), layout="prefix", prefix_level=3,
-                        formats=("bf16", "f32"))
+                        formats=("bf16", "f32"), capacity=N_ + 65536)
         pres = {}
         for pdt in ("bf16", "f32"):
             qps, s = timed(lambda: ptree.query(Qd, rd, dtype=pdt, results_on_device=True,
@@ -670,6 +672,14 @@ def main():
             "device_gb_bf16_rows": round((N_ * 4 + N_ * 2 + ((N_ + 7) >> 3) * 2) * stride_ / 1e9, 2),
             "device_gb_with_f32_rows": round((N_ * 8 + N_ * 2 + ((N_ + 7) >> 3) * 2) * stride_ / 1e9, 2),
             "tree_device_gb": round(rows_tree * stride_ * 7 / 1e9, 2)}
+        if not a.no_serve:
+            # the same continuous-batching server over the prefix layout (its
+            # GEMM tile tuned first), 50k q/s offered, 1% of requests inserts
+            ptree.autotune(Qd, rd, dtype="bf16", stream=stream)
+            rhos = np.array(ds.workload.rhos or (a.rho,), dtype=np.float32)
+            extra = ds.F[np.random.default_rng(8).choice(N, 4096, replace=False)]
+            comparators["prefix_layout"]["serving"] = serve_run(gt, ptree, Q, rhos, 50000.0, 20000,
+                                                                "bf16", inserts=extra)
         ptree.close()
         torch.cuda.empty_cache()
     del Fd
@@ -724,6 +734,15 @@ def main():
         for r in [float(x) for x in a.serve_rates.split(",") if x.strip()]:
             n_req = int(min(200_000, max(20_000, r * 0.4))) if r > 0 else 100_000
             serving.append(serve_run(gt, tree, Q, rhos, r, n_req, a.dtype, inserts=extra))
+        if not pre and a.cutover == -1 and tune is not None:
+            # the server's two schedules at 50k q/s offered, back to back: one
+            # launch per level per step, or each step draining the previous
+            # step's group in one persistent launch
+            serving_schedules = {}
+            for sched in ("levels", "drain"):
+                serving_schedules[sched] = serve_run(gt, tree, Q, rhos, 50000.0, 20000, a.dtype,
+                                                     inserts=extra, seed=5, schedule=sched)
+            serving.append({"schedules_at_50k": serving_schedules})
 
     # the paper's streaming setting, on a tree of its own (after the main tree is freed)
     tree.close()

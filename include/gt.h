@@ -206,9 +206,12 @@ gt_status gt_build(const float *F, int64_t N, int32_t d, const gt_build_opts *op
 /* A GT_LAYOUT_PREFIX tree (opts->layout) is queried by gt_query and
  * gt_query_into (dense GEMM at level c, then one prefix split per kept pool
  * down to the items; cutover must be -1 or c, dtype GT_BF16 or, when kept,
- * GT_F32 for the prefix rows; FP32 prefix rows need d <= 1152), grown by
- * gt_insert, read by gt_read_rows and scored by gt_dense_scores at level c;
- * every other entry point returns GT_EINVAL for it. */
+ * GT_F32 for the prefix rows; FP32 prefix rows need d <= 1152) and by the
+ * server (gt_server_*), grown by gt_insert, tuned by gt_autotune and
+ * gt_set_tuning (the GEMM tile only: its dense level is c and its splits
+ * always use the ring-fed gather), read by gt_read_rows and scored by
+ * gt_dense_scores at level c; gt_exhaustive_tree, gt_pair_bounds and
+ * gt_query_static return GT_EINVAL for it. */
 
 /* Streaming insertion (Sec. 4, "Streaming Setting"): append n_new rows f
  * (n_new x d) as items N .. N+n_new-1 (in the order given), then recompute
@@ -280,7 +283,12 @@ typedef struct gt_autotune_result {
                              query is read through L1 rather than held in
                              registers, or 16: rows fed to the tests through
                              a ring of shared-memory slots by bulk
-                             asynchronous copies (0: the format's default) */
+                             asynchronous copies, or 32: the same gather in
+                             one persistent launch whose warps drain the
+                             dense GEMM's list as a shared work queue, each
+                             carrying the entries it claims down to the
+                             items (subtraction path, cutover 2..5; 0: the
+                             format's default) */
   int32_t tile_n;         /* chosen GEMM tile: 128 (128 queries x 128 pools
                              on one SM), 256 (128 x 256), 512 (256 x 256 on
                              one SM) or 1024 (256 x 256 on a pair of SMs,
@@ -289,7 +297,7 @@ typedef struct gt_autotune_result {
   float ms_cutover[9];    /* stage 1: cutover c = 1..8 on the direct path,
                              default in-flight, tile 256 */
   float ms_cutover_sub[9];/* stage 1: the same on the subtraction path (c >= 2) */
-  float ms_inflight[7];   /* stage 2: codes 1, 2, 4, 9, 10, 12, 16 at the best cutover */
+  float ms_inflight[8];   /* stage 2: codes 1, 2, 4, 9, 10, 12, 16, 32 at the best cutover */
   float ms_tile[4];       /* stage 3: tiles 128, 256, 512, 1024 at the best of both */
   int32_t subtract;       /* 1 if the subtraction path was chosen (stage 1) */
 } gt_autotune_result;
@@ -408,19 +416,44 @@ typedef struct gt_server_opts {
   int64_t scratch_bytes; /* device memory for the level lists (0: 4 GiB) */
   int64_t queue_capacity;/* queued queries held before the pinned queue grows
                             (0: max(4 x max_group, 16384)) */
+  int32_t schedule;      /* how a group moves below the cutover, one of
+                            gt_server_schedule (0: GT_SCHEDULE_AUTO) */
+  int32_t reserved;
 } gt_server_opts;
+
+/* Schedules of the server.
+ *   GT_SCHEDULE_LEVELS  one level per step: every step launches, for each
+ *                       group in flight, the kernel of the level it is at, so
+ *                       a group finishes c + 1 steps after admission and up
+ *                       to c + 1 groups share each step.
+ *   GT_SCHEDULE_DRAIN   each step drains the group admitted the step before
+ *                       in one persistent launch (every level below the
+ *                       cutover and its items, the warps working through the
+ *                       GEMM's list as a shared queue) while it admits the
+ *                       next group: two groups share each step and a group
+ *                       finishes one step after admission.  Needs the
+ *                       subtraction path (sum pools, cutover 2 to 5).
+ *   GT_SCHEDULE_AUTO    GT_SCHEDULE_DRAIN where it applies, else
+ *                       GT_SCHEDULE_LEVELS. */
+typedef enum gt_server_schedule {
+  GT_SCHEDULE_AUTO = 0,
+  GT_SCHEDULE_LEVELS = 1,
+  GT_SCHEDULE_DRAIN = 2
+} gt_server_schedule;
 
 typedef struct gt_server_stats {
   int64_t submitted, admitted, completed, pending, inserted;
   int64_t steps, launches, retries, rechecks, refines;
   int64_t gathered_tests, dense_tests;
   int64_t cutover, max_group;
+  int64_t schedule;      /* the gt_server_schedule in use (LEVELS or DRAIN) */
   double busy_seconds;   /* host wall time spent inside gt_server_step */
 } gt_server_stats;
 
-/* Create a server over tree t (which must keep BF16 rows).  The server owns
- * its device buffers; the tree must outlive it and is updated in place by
- * queued inserts. */
+/* Create a server over tree t (which must keep BF16 rows; a GT_LAYOUT_PREFIX
+ * tree is served at its prefix_level, a GT_POOL_MAXMIN tree is refused).  The
+ * server owns its device buffers; the tree must outlive it and is updated in
+ * place by queued inserts. */
 gt_status gt_server_create(gt_tree *t, const gt_server_opts *opts, gt_server **out);
 /* Queue n queries (host Q n x d, rho n, caller tags n); copied on return. */
 gt_status gt_server_submit(gt_server *s, const float *Q, const float *rho, const int64_t *tags,

@@ -104,6 +104,7 @@ void free_workspace(gt_tree *t) {
   cudaFree(w.thr_accept);
   cudaFree(w.bcnt);
   cudaFree(w.boff);
+  cudaFree(w.drain);
   if (w.hcounters) cudaFreeHost(w.hcounters);
   w = Workspace();
 }
@@ -599,6 +600,14 @@ static gt_status run_search_on(gt_tree *t, const float *Q, int64_t B, const floa
   // with the subtraction path, the items are split the same way (right item
   // tested, left item bounded) where the ring-fed kernel's slots fit
   const bool items_sub = pre || (sub && items_sub_available(t, fmt));
+  // every level below the cutover in one persistent launch (k_drain) when
+  // the tree's tuning chose it
+  const bool drain = !pre && sub && items_sub && t->tuned_g[fmt] == kInflightDrain &&
+                     drain_available(t, fmt, cut);
+  if (drain) {
+    st = ws_reserve_drain(t);
+    if (st != GT_OK) return st;
+  }
 
   const int64_t budget = o.scratch_bytes > 0 ? o.scratch_bytes : default_budget();
   int64_t front_cap = std::max<int64_t>(1 << 10, budget * 7 / 10 / (2 * (int64_t)sizeof(Pair)));
@@ -674,6 +683,16 @@ static gt_status run_search_on(gt_tree *t, const float *Q, int64_t B, const floa
         n_launch += 6;  // thresholds + GEMM + count, scan, scatter, count fix
         first_level = cut - 1;
       }
+      if (drain) {
+        // the GEMM's grouped level-(c-1) list is the work queue
+        tmr.begin(0);
+        launch_drain(t, fmt, cut, reinterpret_cast<const SibPair *>(w.front[(cut - 1) & 1]),
+                     w.counters + (cut - 1), s);
+        tmr.end();
+        n_launch += 1;
+        n_level += 1;
+        first_level = -1;
+      }
       for (int h = first_level; h >= 0; --h) {
         Pair *in = w.front[h & 1];
         Pair *outp = h > 0 ? w.front[(h - 1) & 1] : nullptr;
@@ -702,6 +721,7 @@ static gt_status run_search_on(gt_tree *t, const float *Q, int64_t B, const floa
         n_launch += 1;
         if (h > 0) n_level += 1;
       }
+      if (drain && defer_active(t, fmt)) n_launch += 1;
       if (first_level >= 0 && defer_active(t, fmt)) n_launch += (sub && items_sub) ? 2 : 1;
       tmr.begin(3);
       launch_recheck(t, q0, s);
@@ -1085,10 +1105,10 @@ gt_status gt_pair_bounds(gt_tree *t, int32_t level, int32_t dtype, const float *
 gt_status gt_autotune(gt_tree *t, const float *Q, int64_t B, const float *rho, int32_t dtype,
                       void *stream, gt_autotune_result *out) {
   if (!t || !Q || !rho || B < 1) return set_error(GT_EINVAL, "bad autotune arguments");
-  if (t->layout == GT_LAYOUT_PREFIX) return set_error(GT_EINVAL, "not available for a prefix-layout tree");
+  const bool pre = t->layout == GT_LAYOUT_PREFIX;
   if (dtype < GT_F32 || dtype > GT_FP8 || !(t->formats & (1u << dtype)))
     return set_error(GT_EINVAL, "tree does not keep this row format");
-  if (!dense_available() || !(t->formats & (1u << GT_BF16)) || t->L < 2)
+  if (!dense_available() || !(t->formats & (1u << GT_BF16)) || (!pre && t->L < 2))
     return set_error(GT_EINVAL, "nothing to tune: no dense path for this tree");
   cudaStream_t s = stream ? (cudaStream_t)stream : t->stream;
   gt_autotune_result r;
@@ -1137,14 +1157,43 @@ gt_status gt_autotune(gt_tree *t, const float *Q, int64_t B, const float *rho, i
   };
   const int cmax = std::min(t->L, 8);
   // in-flight codes: 1, 2, 4 tests per warp with the query in registers;
-  // 9, 10, 12 the same with the query read through L1; 16 the ring-fed gather
-  const int gs[7] = {1, 2, 4, 9, 10, 12, 16};
+  // 9, 10, 12 the same with the query read through L1; 16 the ring-fed gather;
+  // 32 the ring-fed gather in one persistent launch for every level below the
+  // cutover (k_drain, subtraction path)
+  const int gs[8] = {1, 2, 4, 9, 10, 12, 16, 32};
   // GEMM tiles: 128 queries x 128 pools, 128 x 256, 256 x 256 on one SM, 256 x
   // 256 on a pair of SMs (codes 128, 256, 512, 1024)
   const int bns[4] = {128, 256, 512, 1024};
   int best_c = 3, best_g = 0, best_bn = 256, best_sub = 0;
   float best = 1e30f;
   gt_status st = GT_OK;
+  if (pre) {
+    // the prefix layout fixes its dense level (prefix_level) and always splits
+    // with the ring-fed gather: only the GEMM tile is free
+    for (int bi = 0; bi < 4 && st == GT_OK; ++bi) {
+      st = run(t->pc, 0, bns[bi], &r.ms_tile[bi]);
+      if (st == GT_OK && r.ms_tile[bi] < best) {
+        best = r.ms_tile[bi];
+        best_bn = bns[bi];
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(l2_flush);
+    if (st != GT_OK) {
+      t->tuned_bn = 0;
+      return st;
+    }
+    if (t->pc <= 8) r.ms_cutover[t->pc] = r.ms_tile[1];
+    t->tuned_bn = best_bn;
+    r.cutover = t->pc;
+    r.inflight = kInflightRing;
+    r.tile_n = best_bn;
+    r.best_ms = best;
+    r.subtract = 0;
+    if (out) *out = r;
+    return GT_OK;
+  }
   // coordinate descent: cutover level with the direct and the subtraction
   // path, then tests in flight, then tile shape
   for (int c = 1; c <= cmax && st == GT_OK; ++c) {
@@ -1166,7 +1215,7 @@ gt_status gt_autotune(gt_tree *t, const float *Q, int64_t B, const float *rho, i
     }
   }
   cur_sub = best_sub ? 1 : -1;
-  for (int gi = 0; gi < 7 && st == GT_OK; ++gi) {
+  for (int gi = 0; gi < 8 && st == GT_OK; ++gi) {
     st = run(best_c, gs[gi], 256, &r.ms_inflight[gi]);
     if (st == GT_OK && r.ms_inflight[gi] < best) {
       best = r.ms_inflight[gi];
@@ -1204,12 +1253,15 @@ gt_status gt_autotune(gt_tree *t, const float *Q, int64_t B, const float *rho, i
 gt_status gt_set_tuning(gt_tree *t, int32_t dtype, int32_t cutover, int32_t inflight,
                         int32_t tile) {
   if (!t || dtype < GT_F32 || dtype > GT_FP8) return set_error(GT_EINVAL, "bad tuning arguments");
-  if (t->layout == GT_LAYOUT_PREFIX) return set_error(GT_EINVAL, "not available for a prefix-layout tree");
+  if (t->layout == GT_LAYOUT_PREFIX && ((cutover > 0 && cutover != t->pc) || inflight > 0))
+    return set_error(GT_EINVAL, "a prefix-layout tree's dense level is its prefix_level and its "
+                                "splits always use the ring-fed gather: only the tile is tuned");
   if (cutover > t->L) return set_error(GT_EINVAL, "cutover above the root level");
-  if (inflight > 0 && inflight != kInflightRing &&
+  if (inflight > 0 && inflight != kInflightRing && inflight != kInflightDrain &&
       !((inflight & ~8) == 1 || (inflight & ~8) == 2 || (inflight & ~8) == 4))
     return set_error(GT_EINVAL, "tests in flight must be 1, 2 or 4 (plus 8 for the L1 query), "
-                                "or 16 for the ring-fed gather");
+                                "16 for the ring-fed gather, or 32 for one persistent launch "
+                                "of every level");
   if (tile > 0 && tile != 128 && tile != 256 && tile != 512 && tile != 1024)
     return set_error(GT_EINVAL, "tile must be 128, 256, 512 or 1024");
   if (cutover >= 0) t->tuned_cut[dtype] = cutover;

@@ -221,7 +221,10 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
 }
 
 // Reserve `n` slots per lane of a list with one atomic per warp; returns the
-// lane's first slot, or 0xffffffff when the list is full (flag raised).
+// lane's first slot (0xffffffff when n is 0).  A list that runs past its
+// capacity raises the overflow flag; the caller writes only the slots below
+// the capacity, so a list that overflowed still has no hole below it (the
+// next pass reads min(count, cap) entries).
 __device__ __forceinline__ uint32_t warp_reserve(uint32_t *count, uint32_t cap, int *flags,
                                                  uint32_t n) {
   const uint32_t incl = warp_incl_scan(n);
@@ -232,10 +235,7 @@ __device__ __forceinline__ uint32_t warp_reserve(uint32_t *count, uint32_t cap, 
   base = __shfl_sync(0xffffffffu, base, 0);
   if (n == 0) return 0xffffffffu;
   const uint32_t pos = base + incl - n;
-  if ((uint64_t)pos + n > cap) {
-    atomicExch(&flags[kFlagOverflow], 1);
-    return 0xffffffffu;
-  }
+  if ((uint64_t)pos + n > cap) atomicExch(&flags[kFlagOverflow], 1);
   return pos;
 }
 
@@ -303,14 +303,14 @@ __device__ __forceinline__ void epilogue_tile(const DenseArgs &a, uint32_t tcol,
         uint32_t pos = warp_reserve(a.out_count, a.out_cap, a.flags, __popc(m_keep));
         if (pos != 0xffffffffu) {
           SibPair *o = reinterpret_cast<SibPair *>(a.out);
-          for (uint32_t mk = m_keep; mk; mk &= mk - 1) {
+          for (uint32_t mk = m_keep; mk; mk &= mk - 1, ++pos) {
             const int i = __ffs(mk) - 1;
             SibPair e;
             e.q = q;
             e.p = m0 + i;
             e.U = __fmul_ru(__uint_as_float(pick32(r, hh, i)), a.cu_up);
             e.pad = pick32(r, hh, i);  // the raw score (the prefix layout's block total)
-            o[pos++] = e;
+            if (pos < a.out_cap) o[pos] = e;
           }
         }
       } else if (a.mode == 0) {
@@ -327,12 +327,14 @@ __device__ __forceinline__ void epilogue_tile(const DenseArgs &a, uint32_t tcol,
             Pair p0;
             p0.q = q;
             p0.j = 2u * m;
-            a.out[pos++] = p0;
+            if (pos < a.out_cap) a.out[pos] = p0;
+            ++pos;
             if (2u * m + 1u < a.n_child) {
               Pair p1;
               p1.q = q;
               p1.j = 2u * m + 1u;
-              a.out[pos++] = p1;
+              if (pos < a.out_cap) a.out[pos] = p1;
+              ++pos;
             }
           }
         }
@@ -346,20 +348,20 @@ __device__ __forceinline__ void epilogue_tile(const DenseArgs &a, uint32_t tcol,
         const uint32_t m_rc = m_keep & ~m_acc;
         uint32_t pos = warp_reserve(a.out_count, a.out_cap, a.flags, __popc(m_acc));
         if (pos != 0xffffffffu) {
-          for (uint32_t mk = m_acc; mk; mk &= mk - 1) {
+          for (uint32_t mk = m_acc; mk; mk &= mk - 1, ++pos) {
             Pair p;
             p.q = q;
             p.j = m0 + __ffs(mk) - 1;
-            a.out[pos++] = p;
+            if (pos < a.out_cap) a.out[pos] = p;
           }
         }
         pos = warp_reserve(a.rchk_count, a.rchk_cap, a.flags, __popc(m_rc));
         if (pos != 0xffffffffu) {
-          for (uint32_t mk = m_rc; mk; mk &= mk - 1) {
+          for (uint32_t mk = m_rc; mk; mk &= mk - 1, ++pos) {
             Pair p;
             p.q = q;
             p.j = m0 + __ffs(mk) - 1;
-            a.rchk[pos++] = p;
+            if (pos < a.rchk_cap) a.rchk[pos] = p;
           }
         }
       }

@@ -97,6 +97,8 @@ struct Workspace {
   float *stage = nullptr;        // host->device staging of inputs
   int64_t stage_bytes = 0;
   uint32_t *hcounters = nullptr; // pinned host mirror of counters + flags
+  void *drain = nullptr;         // k_drain: the warps' private lists
+  int64_t drain_cap = 0;         // (entries of 16 bytes)
 };
 
 // A captured CUDA graph of one micro-batch of the query path, keyed by
@@ -247,6 +249,24 @@ inline int bound_level(const gt_tree *t, int h) {
 inline int ring_batch_for(int64_t b) { return b >= 1024 ? 32 : (b >= 256 ? 16 : 8); }
 // Tests-in-flight code bit selecting the ring-fed gather kernel (k_ring).
 constexpr int kInflightRing = 16;
+// Tests-in-flight code selecting, on the subtraction path, one persistent
+// launch (k_drain) for every level below the cutover instead of one launch
+// per level (the ring-fed gather otherwise).
+constexpr int kInflightDrain = 32;
+// Counter slot of k_drain's work-queue head.
+constexpr int kDrainHeadSlot = kMaxLevels + 4;
+// Whether k_drain serves tree t in format fmt below cutover level cut (the
+// subtraction path of a sum-pooled tree, 2 <= cut <= 5, rows that fit the ring).
+bool drain_available(const gt_tree *t, int fmt, int cut);
+// Device memory for k_drain's per-warp lists (outside any stream capture).
+gt_status ws_reserve_drain(gt_tree *t);
+// All levels below cutover `cut` and the items in one launch: `root` holds the
+// GEMM's level-(cut-1) entries (grouped by query), `root_count` their count.
+// The entries tested at each level h < cut - 1 are added to level_count[h]
+// and the left items tested to *left_count (null: the workspace's level
+// counters and its left-item slot).
+void launch_drain(gt_tree *t, int fmt, int cut, const SibPair *root, const uint32_t *root_count,
+                  cudaStream_t s, uint32_t *level_count = nullptr, uint32_t *left_count = nullptr);
 // Kernel attributes of the level kernels, set once before any stream capture.
 void prepare_level_kernels();
 void launch_level(gt_tree *t, int fmt, int h, int64_t q0, const Pair *in, const uint32_t *in_count,

@@ -70,6 +70,16 @@ struct gt_server {
   // subtraction path (entries of 16 bytes in the level lists) and the
   // subtraction at the items (left items in `left`)
   bool sub = false, items_sub = false;
+  // prefix layout: list h holds entries of level-(h+1) pools (16 bytes, as
+  // on the subtraction path), each split at its midpoint by one prefix row
+  bool pre = false;
+  // one persistent launch (k_drain) takes a group from the GEMM's list to its
+  // decided items: a group is admitted (GEMM) in one step and finished in the
+  // next, so each step drains the group admitted the step before while it
+  // admits the next one
+  bool drain = false;
+  void *drain_buf = nullptr;
+  int64_t drain_cap = 0;
   // per level two lists (parity), results, rechecks, counters, flags
   gt::Pair *lists[gt::kMaxCut][2] = {};
   gt::Pair *gemm_out = nullptr;  // the new group's GEMM survivors before grouping by query
@@ -104,14 +114,17 @@ namespace {
 
 // A view of the tree whose workspace points at the server's buffers.
 // Start of a step: the next-parity list counts of levels 0 .. cut-1, the
-// result, recheck and refine counts, the left-item count and the flags
-// (words 64 ..) start at zero; the current parity's counts are kept.
+// result, recheck and refine counts, the left-item count, the flags (words
+// 64 ..) and k_drain's test counts (words kDrainCounts ..) start at zero; the
+// current parity's counts are kept.
+constexpr int kDrainCounts = 96;  // k_drain: [96 + h] tests at level h, [96 + 8] left items
 __global__ void k_step_reset(uint32_t *counters, int np, int cut) {
   const int i = threadIdx.x;
   if (i < cut) counters[2 * i + np] = 0u;
   if (i < 3) counters[kMaxLevels + i] = 0u;
   if (i == 0) counters[kLeftItemsSlot] = 0u;
   if (i < kFlagCount) counters[64 + i] = 0u;
+  if (i < 9) counters[kDrainCounts + i] = 0u;
 }
 
 gt_tree view_of(gt_server *S, int64_t n_snap, int64_t slot0) {
@@ -137,6 +150,8 @@ gt_tree view_of(gt_server *S, int64_t n_snap, int64_t slot0) {
   w.counters = S->counters;
   w.bcnt = S->bcnt;
   w.boff = S->boff;
+  w.drain = S->drain_buf;
+  w.drain_cap = S->drain_cap;
   v.flags = S->flags;
   return v;
 }
@@ -167,6 +182,17 @@ gt_status server_alloc(gt_server *S) {
   GT_CUDA(cudaMalloc(&S->bcnt, (size_t)(S->slots + 1) * sizeof(int64_t)));
   GT_CUDA(cudaMalloc(&S->boff, (size_t)(S->slots + 1) * sizeof(int64_t)));
   GT_CUDA(cudaMalloc(&S->res, (size_t)S->res_cap * sizeof(Pair)));
+  if (S->drain) {
+    // k_drain's per-warp lists, sized like the batch path's (a tree view
+    // reserves them, then the server keeps the buffer)
+    gt_tree tmp = *S->t;
+    tmp.ws = Workspace();
+    tmp.graphs = nullptr;
+    gt_status st = ws_reserve_drain(&tmp);
+    if (st != GT_OK) return st;
+    S->drain_buf = tmp.ws.drain;
+    S->drain_cap = tmp.ws.drain_cap;
+  }
   GT_CUDA(cudaMalloc(&S->rchk, (size_t)S->rchk_cap * sizeof(Pair)));
   // list counts, result counts and (from word 64) the status flags in one
   // allocation: a step clears them with one launch and reads them back with
@@ -195,6 +221,7 @@ void server_release(gt_server *S) {
   for (int h = 0; h < kMaxCut; ++h)
     for (int p = 0; p < 2; ++p) cudaFree(S->lists[h][p]);
   cudaFree(S->gemm_out); cudaFree(S->left); cudaFree(S->bcnt); cudaFree(S->boff);
+  cudaFree(S->drain_buf);
   cudaFree(S->res); cudaFree(S->rchk); cudaFree(S->counters);
   if (S->hcounters) cudaFreeHost(S->hcounters);
   cudaFree(S->cnt); cudaFree(S->off); cudaFree(S->ids);
@@ -216,8 +243,8 @@ extern "C" {
 gt_status gt_server_create(gt_tree *t, const gt_server_opts *opts, gt_server **out) {
   if (!t || !out) return set_error(GT_EINVAL, "null argument");
   *out = nullptr;
-  if (t->layout == GT_LAYOUT_PREFIX) return set_error(GT_EINVAL, "not available for a prefix-layout tree");
   if (t->split_sign) return set_error(GT_EINVAL, "not available for a GT_POOL_MAXMIN tree");
+  const bool pre = t->layout == GT_LAYOUT_PREFIX;
   gt_server_opts o;
   std::memset(&o, 0, sizeof(o));
   o.dtype = GT_BF16;
@@ -227,17 +254,35 @@ gt_status gt_server_create(gt_tree *t, const gt_server_opts *opts, gt_server **o
     return set_error(GT_EINVAL, "tree does not keep this row format");
   if (!dense_available() || !(t->formats & (1u << GT_BF16)))
     return set_error(GT_EINVAL, "the server needs the dense GEMM path and BF16 rows");
+  if (pre && o.cutover >= 1 && o.cutover != t->pc)
+    return set_error(GT_EINVAL, "a prefix-layout tree's dense level is its prefix_level");
   gt_server *S = new gt_server();
   S->t = t;
   S->s = o.stream ? (cudaStream_t)o.stream : t->stream;
   S->fmt = o.dtype;
   int cut = o.cutover >= 1 ? o.cutover : (t->tuned_cut[o.dtype] > 0 ? t->tuned_cut[o.dtype] : 3);
   cut = std::max(1, std::min(cut, std::min(t->L, kMaxCut)));
+  if (pre) cut = t->pc;  // the level whose pools (the blocks' totals) are stored
   S->cut = cut;
+  S->pre = pre;
   // the subtraction path as gt_query takes it: sum pools, a cutover above
-  // level 1, unless gt_autotune found it slower for this format
-  S->sub = cut >= 2 && t->pooling == GT_POOL_SUM && t->tuned_sub[o.dtype] != -1;
-  S->items_sub = S->sub && items_sub_available(t, o.dtype);
+  // level 1, unless gt_autotune found it slower for this format (the prefix
+  // layout's lists hold entries like the subtraction path's)
+  S->sub = pre || (cut >= 2 && t->pooling == GT_POOL_SUM && t->tuned_sub[o.dtype] != -1);
+  S->items_sub = !pre && S->sub && items_sub_available(t, o.dtype);
+  // one persistent launch for the levels below the cutover, where it applies
+  // (unless the caller asked for one level per step)
+  if (o.schedule < GT_SCHEDULE_AUTO || o.schedule > GT_SCHEDULE_DRAIN) {
+    delete S;
+    return set_error(GT_EINVAL, "unknown schedule");
+  }
+  S->drain = o.schedule != GT_SCHEDULE_LEVELS && !pre && S->items_sub &&
+             drain_available(t, o.dtype, cut);
+  if (o.schedule == GT_SCHEDULE_DRAIN && !S->drain) {
+    delete S;
+    return set_error(GT_EINVAL, "the drain schedule needs the subtraction path of a sum-pooled "
+                                "tree with the cutover at level 2 to 5");
+  }
   S->max_group = o.max_group > 0 ? o.max_group : 4096;
   S->group_stride = S->max_group;
   S->queue_cap = o.queue_capacity;
@@ -354,7 +399,22 @@ gt_status gt_server_step(gt_server *S, int64_t *in_flight) {
     gt_tree v = view_of(S, g.n_snap, 0);
     v.ring_batch = ring_batch_for(g.b);
     const int h = g.level;
-    if (S->sub && h >= 1) {
+    if (S->drain) {
+      // the group admitted last step: every level below the cutover and its
+      // items in one launch, so it finishes in this step
+      launch_drain(&v, S->fmt, cut, reinterpret_cast<const SibPair *>(S->lists[h][p]),
+                   S->counters + 2 * h + p, s, S->counters + kDrainCounts,
+                   S->counters + kDrainCounts + 8);
+    } else if (S->pre) {
+      // the level-(h+1) pools of list h split at their midpoints: the kept
+      // level-h children go to list h-1, or at h = 0 the items are decided
+      if (!launch_prefix(&v, S->fmt, h + 1, reinterpret_cast<const SibPair *>(S->lists[h][p]),
+                         S->counters + 2 * h + p,
+                         h > 0 ? reinterpret_cast<SibPair *>(S->lists[h - 1][np]) : nullptr,
+                         h > 0 ? S->counters + 2 * (h - 1) + np : nullptr, s))
+        return set_error(GT_EINVAL, "FP32 prefix rows this wide do not fit the gather's "
+                                    "shared-memory slots (d <= 1152 fits)");
+    } else if (S->sub && h >= 1) {
       launch_level_sub(&v, S->fmt, h, reinterpret_cast<const SibPair *>(S->lists[h][p]),
                        S->counters + 2 * h + p, S->lists[h - 1][np], S->counters + 2 * (h - 1) + np, s,
                        S->items_sub);
@@ -370,7 +430,7 @@ gt_status gt_server_step(gt_server *S, int64_t *in_flight) {
                    s);
     }
     ++launches;
-    if (h == 0) {
+    if (h == 0 || S->drain) {
       finishing = &g;
       launch_recheck(&v, 0, s);
       ++launches;
@@ -444,7 +504,7 @@ gt_status gt_server_step(gt_server *S, int64_t *in_flight) {
     launches += 7;
   }
   GT_CUDA(cudaGetLastError());
-  GT_CUDA(cudaMemcpyAsync(S->hcounters, S->counters, (64 + kFlagCount) * sizeof(uint32_t),
+  GT_CUDA(cudaMemcpyAsync(S->hcounters, S->counters, 128 * sizeof(uint32_t),
                           cudaMemcpyDeviceToHost, s));
   GT_CUDA(cudaStreamSynchronize(s));
   const uint32_t *hc = S->hcounters;
@@ -466,7 +526,9 @@ gt_status gt_server_step(gt_server *S, int64_t *in_flight) {
   // The new group may put at most list_cap / 2^(c-1) pairs at level c-1:
   // each level below at most doubles, so no older group's list can overflow.
   const uint32_t fresh_pairs = hc[2 * (cut - 1) + np];
-  const uint32_t fresh_lim = (uint32_t)(list_entries(S) >> (cut - 1));
+  // (with k_drain only the GEMM's list is in device lists: the levels below
+  // live in the warps' own lists)
+  const uint32_t fresh_lim = (uint32_t)(S->drain ? list_entries(S) : list_entries(S) >> (cut - 1));
   bool fresh_overflow = b > 0 && fresh_pairs > fresh_lim;
   if (hc[64 + kFlagOverflow]) {
     bool older = hc[kMaxLevels] > (uint32_t)S->res_cap || hc[kMaxLevels + 1] > (uint32_t)S->rchk_cap;
@@ -505,7 +567,14 @@ gt_status gt_server_step(gt_server *S, int64_t *in_flight) {
       g.level -= 1;
     }
   // the finishing group's item tests (its level-0 list, and the left items)
-  if (finishing) S->st.gathered_tests += hc[p] + (S->items_sub ? hc[kLeftItemsSlot] : 0);
+  if (finishing && S->drain) {
+    // its GEMM list and every level k_drain tested
+    S->st.gathered_tests += hc[2 * (cut - 1) + p];
+    for (int h = 0; h + 1 < cut; ++h) S->st.gathered_tests += hc[kDrainCounts + h];
+    S->st.gathered_tests += hc[kDrainCounts + 8];
+  } else if (finishing) {
+    S->st.gathered_tests += hc[p] + (S->items_sub ? hc[kLeftItemsSlot] : 0);
+  }
   if (b > 0) {
     if (fresh_overflow) {
       // the new group's survivors did not fit: leave it queued, admit fewer
@@ -582,6 +651,7 @@ gt_status gt_server_get_stats(const gt_server *S, gt_server_stats *out) {
   out->pending = S->ring_size;
   out->cutover = S->cut;
   out->max_group = S->max_group;
+  out->schedule = S->drain ? GT_SCHEDULE_DRAIN : GT_SCHEDULE_LEVELS;
   return GT_OK;
 }
 

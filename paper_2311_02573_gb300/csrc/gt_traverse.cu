@@ -111,7 +111,9 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
 }
 
 // Append `n` (0..2) pairs per lane to list `out` with one atomic per warp.
-// Returns false (and raises the overflow flag) if the list is full.
+// A list that runs past its capacity raises the overflow flag; the pairs
+// below the capacity are still written, so it has no hole below it (the next
+// pass reads min(count, cap) pairs; the call then retries with fewer queries).
 __device__ __forceinline__ void warp_append(Pair *out, uint32_t *count, uint32_t cap, int *flags,
                                             uint32_t n, Pair a, Pair b) {
   const uint32_t incl = warp_incl_scan(n);
@@ -124,6 +126,7 @@ __device__ __forceinline__ void warp_append(Pair *out, uint32_t *count, uint32_t
   const uint32_t pos = base + incl - n;
   if ((uint64_t)pos + n > cap) {
     atomicExch(&flags[kFlagOverflow], 1);
+    if (pos < cap) out[pos] = a;   // n == 2 with only the first below the capacity
     return;
   }
   out[pos] = a;
@@ -232,16 +235,22 @@ __device__ __forceinline__ float row_dot(const uint4 (&w)[KV], const float *qreg
 // the accept tests; the constants are make_bound's, the FP8 scale and the
 // e4m3 subnormal term applied here).
 template <int FMT>
-__device__ __forceinline__ void test_bounds(const LevelArgs &a, float acc, uint32_t j, float qn1,
-                                            float &U, float &Lo) {
+__device__ __forceinline__ void test_bounds_scaled(const LevelArgs &a, float acc, float sc, float qn1,
+                                                   float &U, float &Lo) {
   float tq = 0.f;
   if (FMT == GT_FP8) {
-    const float sc = a.scales[j];
     acc *= sc;                      // exact: sc is a power of two
     tq = sc * 0x1p-10f * qn1;       // half the e4m3 subnormal spacing, times |q|_1
   }
   U = fmaf(acc, a.bd.cu, tq * a.bd.ct_up);
   Lo = (acc * a.bd.cl - tq * a.bd.ct_lo) * (1.f - 0x1p-22f);
+}
+
+// The same with row j's FP8 scale read here.
+template <int FMT>
+__device__ __forceinline__ void test_bounds(const LevelArgs &a, float acc, uint32_t j, float qn1,
+                                            float &U, float &Lo) {
+  test_bounds_scaled<FMT>(a, acc, FMT == GT_FP8 ? a.scales[j] : 1.f, qn1, U, Lo);
 }
 
 // FP32 re-score of item row j with the query entries the warp holds (the
@@ -515,19 +524,23 @@ __device__ __forceinline__ void sub_emit(const LevelArgs &a, void *out_v, const 
       uint32_t pos = b0 + incl - tot;
       Pair *out = reinterpret_cast<Pair *>(out_v);
       if (tot) {
-        if ((uint64_t)pos + tot > a.out_cap) {
-          atomicExch(&a.flags[kFlagOverflow], 1);
-        } else {
-          Pair x;
-          x.q = e.q;
-          if (kl) {
-            x.j = 2u * c_l; out[pos++] = x;
-            if (2u * c_l + 1u < a.n_child) { x.j = 2u * c_l + 1u; out[pos++] = x; }
-          }
-          if (kr) {
-            x.j = 2u * c_r; out[pos++] = x;
-            if (2u * c_r + 1u < a.n_child) { x.j = 2u * c_r + 1u; out[pos++] = x; }
-          }
+        // past the capacity: the overflow flag, and only the pairs below it
+        // written (no hole below the capacity)
+        if ((uint64_t)pos + tot > a.out_cap) atomicExch(&a.flags[kFlagOverflow], 1);
+        const uint32_t cap = a.out_cap;
+        Pair x;
+        x.q = e.q;
+        if (kl) {
+          x.j = 2u * c_l;
+          if (pos < cap) out[pos] = x;
+          ++pos;
+          if (2u * c_l + 1u < a.n_child) { x.j = 2u * c_l + 1u; if (pos < cap) out[pos] = x; ++pos; }
+        }
+        if (kr) {
+          x.j = 2u * c_r;
+          if (pos < cap) out[pos] = x;
+          ++pos;
+          if (2u * c_r + 1u < a.n_child) { x.j = 2u * c_r + 1u; if (pos < cap) out[pos] = x; ++pos; }
         }
       }
     }
@@ -542,15 +555,12 @@ __device__ __forceinline__ void sub_emit(const LevelArgs &a, void *out_v, const 
       uint32_t pos = b0 + incl - tot;
       SibPair *out = reinterpret_cast<SibPair *>(out_v);
       if (tot) {
-        if ((uint64_t)pos + tot > a.out_cap) {
-          atomicExch(&a.flags[kFlagOverflow], 1);
-        } else {
-          SibPair x;
-          x.q = e.q;
-          x.pad = 0;
-          if (kl) { x.p = c_l; x.U = my_ul; out[pos++] = x; }
-          if (kr) { x.p = c_r; x.U = my_ur; out[pos++] = x; }
-        }
+        if ((uint64_t)pos + tot > a.out_cap) atomicExch(&a.flags[kFlagOverflow], 1);
+        SibPair x;
+        x.q = e.q;
+        x.pad = 0;
+        if (kl) { x.p = c_l; x.U = my_ul; if (pos < a.out_cap) out[pos] = x; ++pos; }
+        if (kr) { x.p = c_r; x.U = my_ur; if (pos < a.out_cap) out[pos] = x; }
       }
     }
   }
@@ -575,14 +585,18 @@ __device__ __forceinline__ void pre_emit(const LevelArgs &a, void *out_v, const 
   uint32_t pos = b0 + incl - tot;
   SibPair *out = reinterpret_cast<SibPair *>(out_v);
   if (!tot) return;
-  if ((uint64_t)pos + tot > a.out_cap) {
-    atomicExch(&a.flags[kFlagOverflow], 1);
-    return;
-  }
+  if ((uint64_t)pos + tot > a.out_cap) atomicExch(&a.flags[kFlagOverflow], 1);
   SibPair x;
   x.q = e.q;
-  if (kl) { x.p = 2u * e.p; x.U = e.U; x.pad = __float_as_uint(my_mid); out[pos++] = x; }
-  if (kr) { x.p = 2u * e.p + 1u; x.U = my_mid; x.pad = e.pad; out[pos++] = x; }
+  if (kl) {
+    x.p = 2u * e.p; x.U = e.U; x.pad = __float_as_uint(my_mid);
+    if (pos < a.out_cap) out[pos] = x;
+    ++pos;
+  }
+  if (kr) {
+    x.p = 2u * e.p + 1u; x.U = my_mid; x.pad = e.pad;
+    if (pos < a.out_cap) out[pos] = x;
+  }
 }
 
 // Subtraction path, level h >= 1.  Entry (q, p, U_p): the children of parent
@@ -894,15 +908,26 @@ __global__ void __launch_bounds__(32 * kRingWarps, 1)
     uint32_t m_c = 0;            // MODE 4: the left item is tested next
     uint32_t m_d = 0;            // FP8 leaves: re-scored by the BF16 pass
     float my_ul = 0.f, my_ur = 0.f;
-    // The per-pair loop only gathers and scores: wait for the row, dot
-    // product, refill the slot, warp sum.  The score of pair i is kept by
-    // lane i, and after the batch every lane decides its own pair (the
-    // bounds, the subtraction, the prune / accept tests); the few leaf
-    // re-scores then run warp-wide, one item at a time.
+    // At the pool levels (modes 0, 2, 3, 5) the per-pair loop only gathers
+    // and scores: wait for the row, dot product, refill the slot, warp sum.
+    // The score of pair i is kept by lane i, and after the batch every lane
+    // decides its own pair (the bounds, the subtraction, the prune test).  At
+    // the items (modes 1, 4) each pair is decided in the loop, with the
+    // query that is loaded for it: a straddling score is re-scored there and
+    // then, while the ring's next copies are in flight.
+    constexpr bool PER_LANE = MODE != 1 && MODE != 4;
     float my_acc = 0.f;
+    // this lane's pair's query terms (and FP8 row scale), loaded ahead of the
+    // loop so that their latency hides behind it
+    const bool mine = (uint32_t)lane < len_cur;
+    const float qn1_l = (PER_LANE && !PRE && mine) ? a.qn1[e_cur.q] : 0.f;
+    const float rho_l = (PER_LANE && mine) ? a.rho[e_cur.q] : INFINITY;
+    const float sc_l =
+        (FMT == GT_FP8 && PER_LANE && !PRE && mine && r_cur != kNoRow) ? a.scales[r_cur] : 1.f;
     for (uint32_t i = 0; i < len_cur; ++i, ++t) {
       const uint32_t q = __shfl_sync(FULL, e_cur.q, i);
-      const bool has = __shfl_sync(FULL, r_cur, i) != kNoRow;
+      const uint32_t rowi = __shfl_sync(FULL, r_cur, i);
+      const bool has = rowi != kNoRow;
       if (q != cur_q) load_query(q);
       const bool good = ring_wait(full0 + 8u * k, ph, a.expire ? 0ull : kRingWaitNs);
       if (!__all_sync(FULL, good)) {
@@ -944,18 +969,30 @@ __global__ void __launch_bounds__(32 * kRingWarps, 1)
         ph ^= 1u;
       }
       acc = warp_sum(acc);
-      if ((uint32_t)lane == i) my_acc = acc;
+      if (MODE == 1) {
+        decide<FMT, KV, true, false>(a, acc, rowi, qn1, rho, qreg, nullptr, (int)i, m_a, m_b, m_d,
+                                     n_refine);
+      } else if (MODE == 4) {
+        // the right item decided; the left item's bound is the pool's minus
+        // the right item's lower bound
+        const float Up = __shfl_sync(FULL, e_cur.U, i);
+        float Ul = Up, Ur = 0.f;
+        if (has) {
+          decide<FMT, KV, true, false>(a, acc, rowi, qn1, rho, qreg, nullptr, (int)i, m_a, m_b, m_d,
+                                       n_refine);
+          sub_test<FMT>(a, acc, rowi, qn1, Up, Ul, Ur);
+        }
+        if (Ul >= rho) m_c |= 1u << i;
+      } else if ((uint32_t)lane == i) {
+        my_acc = acc;
+      }
     }
     if (!ok) break;
-    if (!PRE) {
-      // this lane's pair: its query's bound terms, the gathered row's score
-      // and bounds
-      const bool mine = (uint32_t)lane < len_cur;
+    if (!PRE && PER_LANE) {
+      // this lane's pair: the gathered row's score and bounds
       const bool has = mine && r_cur != kNoRow;
-      const float qn1_l = mine ? a.qn1[e_cur.q] : 0.f;
-      const float rho_l = mine ? a.rho[e_cur.q] : INFINITY;
       float U = 0.f, Lo = 0.f;
-      if (has) test_bounds<FMT>(a, my_acc, r_cur, qn1_l, U, Lo);
+      if (has) test_bounds_scaled<FMT>(a, my_acc, sc_l, qn1_l, U, Lo);
       // subtraction: the left child's exact score is the parent's minus the
       // right child's, so Ul = U_parent - L_right (rounded up) bounds it.  The
       // last row of a level is the one pool an insert can extend after its
@@ -972,32 +1009,6 @@ __global__ void __launch_bounds__(32 * kRingWarps, 1)
         m_b = __ballot_sync(FULL, has && U >= rho_l);
         my_ul = Ul;
         my_ur = U;
-      } else {
-        // the gathered item: 0 pruned, 1 accepted, 2 FP64 recheck, 3 re-score
-        // here, 4 re-scored from its BF16 row by the pass after this kernel
-        int c = 0;
-        if (has && U >= rho_l) {
-          if (a.no_accept) c = 2;
-          else if (Lo >= rho_l) c = 1;
-          else if (FMT == GT_F32) c = 2;
-          else if (FMT == GT_FP8 && a.rows16 && a.defer) c = 4;
-          else c = 3;
-        }
-        if (MODE == 4) m_c = __ballot_sync(FULL, mine && Ul >= rho_l);
-        uint32_t need = __ballot_sync(FULL, c == 3);
-        while (need) {
-          const int j = __ffs(need) - 1;
-          need &= need - 1u;
-          const uint32_t qj = __shfl_sync(FULL, e_cur.q, j);
-          if (qj != cur_q) load_query(qj);
-          const int r = leaf_rescore<FMT, KV, false>(a, __shfl_sync(FULL, r_cur, j), rho, qreg,
-                                                     nullptr, n_refine);
-          if (lane == j) c = r;
-        }
-        m_a = __ballot_sync(FULL, c == 1);
-        m_b = __ballot_sync(FULL, c == 2);
-        m_d = __ballot_sync(FULL, c == 4);
-        n_refine += (uint32_t)__popc(m_d);
       }
     }
     if (PRE) {
@@ -1008,13 +1019,11 @@ __global__ void __launch_bounds__(32 * kRingWarps, 1)
       // test.  Each bound holds the exact S (the row format's and the FP32
       // accumulation's error terms), so a difference of bounds, rounded
       // outward, holds a child's exact score.
-      const bool mine = (uint32_t)lane < len_cur;
       const bool hasr = r_cur != kNoRow;
       const uint32_t bmask = (1u << a.pre_c) - 1u;
       const uint32_t lo = e_cur.p << a.pre_h;
       const uint32_t hi = min(lo + (1u << a.pre_h), a.n_items);
       const float s_lo = e_cur.U, s_hi = __uint_as_float(e_cur.pad);
-      const float rho_l = mine ? a.rho[e_cur.q] : INFINITY;
       float lu = 0.f, ld = 0.f, hu, hd, mu = 0.f, md = 0.f;
       if (lo & bmask) test_bounds<FMT>(a, s_lo, 0u, 0.f, lu, ld);
       if ((hi & bmask) == 0u || hi == a.n_items) {
@@ -1125,6 +1134,338 @@ __global__ void __launch_bounds__(32 * kRingWarps, 1)
   }
   raise_stray(a, stray);
   if (LEAF && n_refine && lane == 0) atomicAdd(a.refine_count, n_refine);
+}
+
+// ---- One persistent launch for every level below the cutover ---------------
+// k_drain: the warps of one persistent grid drain a shared work queue, the
+// list of (query, pool, bound) entries the dense GEMM leaves at level c-1
+// (grouped by query).  A warp claims 32 consecutive entries at a time and
+// carries their subtrees down to the items itself, level by level, in
+// private lists: the entries' right children are gathered (the ring of
+// k_ring) and tested, the left ones bounded by subtraction (Algorithm 1's
+// sim - rsim, as an upper bound), the survivors become the warp's next list
+// (at most twice as long), and at the items the right item of each surviving
+// level-1 pool is decided, then the left items that their bound keeps.  All
+// levels of the batch run in this one launch; a warp never waits for another
+// (the queue is complete before the launch), so the only waits are the
+// ring's bounded ones.  Levels whose lists are short no longer pay a launch
+// and a tail each.
+constexpr int kDrainMaxCut = 5;        // lists of 32 << (c - 1) entries per warp
+
+struct DrainLevel {
+  int64_t row0;      // first row of the level (row index into the format's rows)
+  uint32_t n_rows;   // rows at the level
+  Bound bd;          // the level's bound constants (row format, FP32 pool sums)
+};
+
+// (the gathered rows and FP8 scales, from row 0 of level 0, are the
+// LevelArgs' rows and scales)
+struct DrainArgs {
+  DrainLevel lvl[kDrainMaxCut];
+  const SibPair *root;       // the queue: entries of level-c pools (children at c - 1)
+  const uint32_t *root_count;
+  uint32_t root_cap;
+  uint32_t *head;            // next queue position to claim (zero at launch)
+  uint32_t *level_count;     // [h]: entries tested at level h < c - 1
+  uint32_t *left_count;      // left items tested
+  SibPair *scratch;          // per warp: two lists of wcap entries, then wcap item pairs
+  uint32_t wcap;
+  int cut;
+};
+
+template <int FMT, int KV>
+__global__ void __launch_bounds__(32 * kRingWarps, 1)
+    k_drain(const LevelArgs a, const DrainArgs g, uint32_t depth, uint32_t slot_bytes) {
+  constexpr int EPV = RowFmt<FMT>::EPV;
+  constexpr uint32_t kNoRow = 0xffffffffu;
+  extern __shared__ __align__(128) uint8_t ring_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t sbase = (smem_addr(ring_raw) + 127u) & ~127u;
+  const uint8_t *gbase = ring_raw + (sbase - smem_addr(ring_raw));
+  // after the slots and their barriers: the block's test counts per level,
+  // then of left items (all shared memory is dynamic, so the kernel may
+  // take the same opt-in size as k_ring)
+  uint32_t *blk_count = reinterpret_cast<uint32_t *>(
+      const_cast<uint8_t *>(gbase) + (size_t)kRingWarps * depth * (slot_bytes + 8u));
+  if (threadIdx.x <= kDrainMaxCut) blk_count[threadIdx.x] = 0u;
+  __syncthreads();
+  const uint32_t slot0 = sbase + (uint32_t)warp * depth * slot_bytes;
+  const uint8_t *gslot0 = gbase + (size_t)warp * depth * slot_bytes;
+  const uint32_t full0 = sbase + kRingWarps * depth * slot_bytes + (uint32_t)warp * depth * 8u;
+  const uint32_t copy_bytes = (uint32_t)a.nvec * 16u;
+  if (lane == 0) {
+    for (uint32_t k = 0; k < depth; ++k) ring_bar_init(full0 + 8u * k, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  const uint32_t gw = blockIdx.x * kRingWarps + (uint32_t)warp;
+  SibPair *listA = g.scratch + (size_t)gw * (2u * g.wcap + (g.wcap + 1u) / 2u);
+  SibPair *listB = listA + g.wcap;
+  Pair *left = reinterpret_cast<Pair *>(listB + g.wcap);
+  const uint32_t n_root = min(*g.root_count, g.root_cap);
+
+  float qreg[KV * EPV];
+  uint32_t cur_q = 0xffffffffu;
+  float qn1 = 0.f, rho = 0.f;
+  uint32_t n_refine = 0;
+  bool ok = true, stray = false;
+  auto load_query = [&](uint32_t q) {
+    cur_q = q;
+    const float4 *qrow = reinterpret_cast<const float4 *>(a.qf32 + (size_t)q * a.qstride);
+#pragma unroll
+    for (int kk = 0; kk < KV; ++kk) {
+      const int v = lane + 32 * kk;
+#pragma unroll
+      for (int x = 0; x < EPV / 4; ++x) {
+        const float4 y = v < a.nvec ? qrow[v * (EPV / 4) + x] : make_float4(0.f, 0.f, 0.f, 0.f);
+        qreg[kk * EPV + 4 * x + 0] = y.x;
+        qreg[kk * EPV + 4 * x + 1] = y.y;
+        qreg[kk * EPV + 4 * x + 2] = y.z;
+        qreg[kk * EPV + 4 * x + 3] = y.w;
+      }
+    }
+    qn1 = a.qn1[q];
+    rho = a.rho[q];
+  };
+  // the ring: stream position t is the pair being tested (slot k, phase
+  // parity ph); copies are started in stream order up to t + depth - 1
+  uint32_t t = 0, k = 0, ph = 0, t_issued = 0, k_iss = 0;
+  auto issue = [&](const uint8_t *rows_lvl, uint32_t row) {
+    if (lane == 0) {
+      const uint32_t bar = full0 + 8u * k_iss;
+      if (row != kNoRow) {
+        ring_expect(bar, copy_bytes);
+        ring_copy(slot0 + k_iss * slot_bytes, rows_lvl + (size_t)row * a.row_bytes, copy_bytes, bar);
+      } else {
+        ring_arrive(bar);
+      }
+    }
+    ++t_issued;
+    if (++k_iss == depth) k_iss = 0;
+  };
+
+  // One list of n entries (src) at level h, in batches of 32.  kind 0: the
+  // entries are pools of level h + 1 (h >= 1), their children at level h are
+  // tested and the kept ones appended to dst as entries for level h - 1;
+  // kind 1 (h = 0): the entries are level-1 pools, the right item is decided
+  // and the left item appended to `left` when its bound keeps it; kind 2: the
+  // item pairs of `left` are decided.
+  auto run_list = [&](int kind, int h, const SibPair *src, const Pair *srcp, uint32_t n, SibPair *dst,
+                      uint32_t &dst_n) {
+    const DrainLevel L = g.lvl[h];
+    const uint8_t *rows_lvl = a.rows + (size_t)L.row0 * a.row_bytes;
+    const float *scales_lvl = FMT == GT_FP8 ? a.scales + L.row0 : nullptr;
+    auto fetch = [&](uint32_t b0, SibPair &e, uint32_t &row) {
+      const uint32_t idx = b0 + (uint32_t)lane;
+      row = kNoRow;
+      e.q = 0xffffffffu; e.p = 0; e.U = 0.f; e.pad = 0;
+      if (b0 >= n || idx >= n) return;
+      if (kind == 2) {
+        const Pair x = srcp[idx];
+        e.q = x.q; e.p = x.j;
+        row = x.j;
+      } else {
+        e = src[idx];
+        const uint32_t r = 2u * e.p + 1u;
+        if (r < L.n_rows) row = r;
+      }
+    };
+    SibPair e_cur, e_nxt;
+    uint32_t r_cur, r_nxt;
+    fetch(0, e_cur, r_cur);
+    fetch(32, e_nxt, r_nxt);
+    if (lane == 0) atomicAdd(&blk_count[kind == 2 ? kDrainMaxCut : h], n);
+    for (uint32_t b0 = 0; b0 < n && ok; b0 += 32) {
+      const uint32_t len = min(32u, n - b0);
+      const uint32_t len_nxt = b0 + 32 < n ? min(32u, n - b0 - 32) : 0u;
+      // row of stream position x >= t0 (this batch starts at t0, then the
+      // next batch of the list)
+      const uint32_t t0 = t;
+      auto row_at = [&](uint32_t x, bool &have) -> uint32_t {
+        const uint32_t rel = x - t0;
+        have = true;
+        if (rel < len) return __shfl_sync(FULL, r_cur, rel);
+        if (len == 32 && rel - 32 < len_nxt) return __shfl_sync(FULL, r_nxt, rel - 32);
+        have = false;
+        return kNoRow;
+      };
+      // the first pairs of a list were not prefetched: start their copies
+      // (none with a.expire: a failure-detection test)
+      while (!a.expire && t_issued < t + depth) {
+        bool have;
+        const uint32_t row = row_at(t_issued, have);
+        if (!have) break;
+        issue(rows_lvl, row);
+      }
+      const bool mine = (uint32_t)lane < len;
+      const float qn1_l = mine ? a.qn1[e_cur.q] : 0.f;
+      const float rho_l = mine ? a.rho[e_cur.q] : INFINITY;
+      const float sc_l = (FMT == GT_FP8 && mine && r_cur != kNoRow) ? scales_lvl[r_cur] : 1.f;
+      float my_acc = 0.f;
+      for (uint32_t i = 0; i < len; ++i, ++t) {
+        const uint32_t q = __shfl_sync(FULL, e_cur.q, i);
+        const bool has = __shfl_sync(FULL, r_cur, i) != kNoRow;
+        if (q != cur_q) load_query(q);
+        const bool good = ring_wait(full0 + 8u * k, ph, a.expire ? 0ull : kRingWaitNs);
+        if (!__all_sync(FULL, good)) {
+          ok = false;
+          break;
+        }
+        uint4 w[KV];
+        const uint4 *rowp = reinterpret_cast<const uint4 *>(gslot0 + (size_t)k * slot_bytes);
+#pragma unroll
+        for (int kk = 0; kk < KV; ++kk) {
+          const int v = lane + 32 * kk;
+          w[kk] = (has && v < a.nvec) ? rowp[v] : make_uint4(0u, 0u, 0u, 0u);
+        }
+        float acc = row_dot<FMT, KV, false>(w, qreg, nullptr, a.nvec);
+        // the slot's next contents arrive through the async proxy: order this
+        // warp's reads of it before the copy that refills it
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (!a.expire && t_issued == t + depth) {
+          bool have;
+          const uint32_t row = row_at(t + depth, have);
+          if (have) issue(rows_lvl, row);
+        }
+        if (++k == depth) {
+          k = 0;
+          ph ^= 1u;
+        }
+        acc = warp_sum(acc);
+        if ((uint32_t)lane == i) my_acc = acc;
+      }
+      if (!ok) break;
+      // every lane decides its own pair
+      const bool has = mine && r_cur != kNoRow;
+      float U = 0.f, Lo = 0.f;
+      if (has) {
+        float acc = my_acc, tq = 0.f;
+        if (FMT == GT_FP8) {
+          acc *= sc_l;
+          tq = sc_l * 0x1p-10f * qn1_l;
+        }
+        U = fmaf(acc, L.bd.cu, tq * L.bd.ct_up);
+        Lo = (acc * L.bd.cl - tq * L.bd.ct_lo) * (1.f - 0x1p-22f);
+      }
+      // subtraction (kinds 0, 1): the left child's bound; the last row of a
+      // level is not subtracted (an insert may have extended it since the
+      // parent's bound was taken)
+      float Ul = e_cur.U;
+      if (kind != 2 && has) Ul = __fsub_ru(e_cur.U, r_cur + 1u >= L.n_rows ? 0.f : fmaxf(Lo, 0.f));
+      if (kind == 0) {
+        const bool kl = mine && Ul >= rho_l, kr = has && U >= rho_l;
+        const uint32_t cntl = (kl ? 1u : 0u) + (kr ? 1u : 0u);
+        const uint32_t incl = warp_incl_scan(cntl);
+        uint32_t pos = dst_n + incl - cntl;
+        SibPair x;
+        x.q = e_cur.q;
+        x.pad = 0;
+        if (kl) { x.p = 2u * e_cur.p; x.U = Ul; dst[pos++] = x; }
+        if (kr) { x.p = 2u * e_cur.p + 1u; x.U = U; dst[pos++] = x; }
+        dst_n += __shfl_sync(FULL, incl, 31);
+      } else {
+        // the gathered item: 0 pruned, 1 accepted, 2 FP64 recheck, 3 re-score
+        // here, 4 re-scored from its BF16 row by the pass after this kernel
+        int c = 0;
+        if (has && U >= rho_l) {
+          if (Lo >= rho_l) c = 1;
+          else if (FMT == GT_F32) c = 2;
+          else if (FMT == GT_FP8 && a.rows16 && a.defer) c = 4;
+          else c = 3;
+        }
+        if (kind == 1) {
+          // the left item of a kept level-1 pool goes to `left` for a direct test
+          const bool kl = mine && Ul >= rho_l;
+          const uint32_t incl = warp_incl_scan(kl ? 1u : 0u);
+          if (kl) {
+            Pair x;
+            x.q = e_cur.q;
+            x.j = 2u * e_cur.p;
+            left[dst_n + incl - 1u] = x;
+          }
+          dst_n += __shfl_sync(FULL, incl, 31);
+        }
+        uint32_t need = __ballot_sync(FULL, c == 3);
+        while (need) {
+          const int j = __ffs(need) - 1;
+          need &= need - 1u;
+          const uint32_t qj = __shfl_sync(FULL, e_cur.q, j);
+          if (qj != cur_q) load_query(qj);
+          const int r = leaf_rescore<FMT, KV, false>(a, __shfl_sync(FULL, r_cur, j), rho, qreg,
+                                                     nullptr, n_refine);
+          if (lane == j) c = r;
+        }
+        Pair it;
+        it.q = e_cur.q;
+        it.j = r_cur;
+        warp_append(a.res, a.res_count, a.res_cap, a.flags, c == 1 ? 1u : 0u, it, it);
+        warp_append(a.rchk, a.rchk_count, a.rchk_cap, a.flags, c == 2 ? 1u : 0u, it, it);
+        if (FMT == GT_FP8) {
+          const uint32_t m_d = __ballot_sync(FULL, c == 4);
+          if (m_d) {
+            warp_append(a.defer, a.defer_count, a.defer_cap, a.flags, c == 4 ? 1u : 0u, it, it);
+            n_refine += (uint32_t)__popc(m_d);
+          }
+        }
+      }
+      __syncwarp();   // the warp's list writes before its reads of them
+      e_cur = e_nxt;
+      r_cur = r_nxt;
+      fetch(b0 + 64, e_nxt, r_nxt);
+    }
+  };
+
+  while (ok) {
+    // claim the next 32 entries of the queue
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(g.head, 32u);
+    base = __shfl_sync(FULL, base, 0);
+    if (base >= n_root) break;
+    const uint32_t cnt = min(32u, n_root - base);
+    // a queue entry naming a query or a row outside its buffers can only
+    // come from a corrupted list: flagged, and its subtree left out
+    bool bad = false;
+    if ((uint32_t)lane < cnt) {
+      const SibPair e = g.root[base + lane];
+      bad = !(e.q < a.q_lim && 2u * e.p < g.lvl[g.cut - 1].n_rows);
+    }
+    if (__any_sync(FULL, bad)) {
+      stray = true;
+      continue;
+    }
+    uint32_t n = cnt;
+    const SibPair *src = g.root + base;
+    SibPair *dst = listA;
+    for (int h = g.cut - 1; h >= 1 && ok; --h) {
+      uint32_t dn = 0;
+      run_list(0, h, src, nullptr, n, dst, dn);
+      src = dst;
+      dst = dst == listA ? listB : listA;
+      n = dn;
+    }
+    uint32_t nl = 0;
+    if (ok) run_list(1, 0, src, nullptr, n, nullptr, nl);
+    uint32_t unused = 0;
+    if (ok) run_list(2, 0, nullptr, left, nl, nullptr, unused);
+  }
+  if (!ok && lane == 0) atomicExch(&a.flags[kFlagTimeout], 1);
+  // every copy this warp started has landed before it exits
+  if (lane == 0) {
+    const uint64_t t0 = ring_now();
+    for (uint32_t tt = t_issued > depth ? t_issued - depth : 0; tt < t_issued; ++tt) {
+      const uint32_t ks = tt % depth, pk = (tt / depth) & 1u;
+      while (!ring_test(full0 + 8u * ks, pk) && ring_now() - t0 < kRingWaitNs) {
+      }
+    }
+  }
+  raise_stray(a, stray);
+  if (n_refine && lane == 0) atomicAdd(a.refine_count, n_refine);
+  __syncthreads();
+  if (threadIdx.x < (unsigned)g.cut - 1u && blk_count[threadIdx.x])
+    atomicAdd(&g.level_count[threadIdx.x], blk_count[threadIdx.x]);
+  if (threadIdx.x == 0 && blk_count[kDrainMaxCut])
+    atomicAdd(g.left_count, blk_count[kDrainMaxCut]);
 }
 
 // Diagnostic twin of the level kernels' test: one warp per given (query,
@@ -1609,12 +1950,29 @@ void ring_attr_modes() {
   ring_attr<FMT, KV, 4>();
 }
 
+template <int FMT, int KV>
+void drain_attr() {
+  cudaFuncSetAttribute(k_drain<FMT, KV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       ring_smem_max());
+}
+
 // Slots per warp of k_ring for rows of nvec 16-byte vectors: as many as fit
 // in the block's shared memory, at most kRingMaxDepth; 0 (no ring) below 2.
 uint32_t ring_depth(int nvec, uint32_t *slot_bytes) {
   *slot_bytes = ((uint32_t)nvec * 16u + 127u) & ~127u;
   const uint32_t d = (uint32_t)(ring_smem_max() - 256) / (kRingWarps * (*slot_bytes + 8u));
   return d >= 2 ? std::min<uint32_t>(d, kRingMaxDepth) : 0u;
+}
+
+template <int FMT, int KV>
+bool launch_drain_t(const LevelArgs &a, const DrainArgs &g, int sm_count, cudaStream_t s) {
+  uint32_t slot = 0;
+  const uint32_t depth = ring_depth(a.nvec, &slot);
+  if (!depth) return false;
+  // the ring, its barriers, the alignment pad and the block's counters
+  const size_t smem = (size_t)kRingWarps * depth * (slot + 8u) + 256u;
+  k_drain<FMT, KV><<<sm_count, 32 * kRingWarps, smem, s>>>(a, g, depth, slot);
+  return true;
 }
 
 template <int FMT, int KV, int MODE>
@@ -1790,7 +2148,102 @@ void prepare_level_kernels() {
   ring_attr<GT_BF16, 4, 6>();
   ring_attr<GT_BF16, 8, 5>();
   ring_attr<GT_BF16, 8, 6>();
+  drain_attr<GT_F32, 8>();
+  drain_attr<GT_F32, 16>();
+  drain_attr<GT_BF16, 4>();
+  drain_attr<GT_BF16, 8>();
+  drain_attr<GT_FP8, 2>();
+  drain_attr<GT_FP8, 4>();
   cudaGetLastError();
+}
+
+bool drain_available(const gt_tree *t, int fmt, int cut) {
+  uint32_t slot = 0;
+  return cut >= 2 && cut <= kDrainMaxCut && t->layout == GT_LAYOUT_TREE &&
+         t->pooling == GT_POOL_SUM && !t->split_sign &&
+         ring_depth((int)((t->d * entry_bytes(fmt) + 15) / 16), &slot) > 0;
+}
+
+gt_status ws_reserve_drain(gt_tree *t) {
+  Workspace &w = t->ws;
+  // per warp: two lists of 32 << (c - 1) entries and the left items, for c
+  // up to kDrainMaxCut
+  const int64_t wcap = (int64_t)32 << (kDrainMaxCut - 1);
+  const int64_t per_warp = 2 * wcap + (wcap + 1) / 2;
+  const int64_t n = (int64_t)t->sm_count * kRingWarps * per_warp;
+  if (w.drain && w.drain_cap >= n) return GT_OK;
+  cudaFree(w.drain);
+  w.drain = nullptr;
+  w.drain_cap = 0;
+  GT_CUDA(cudaMalloc(&w.drain, (size_t)n * sizeof(SibPair)));
+  w.drain_cap = n;
+  return GT_OK;
+}
+
+static void launch_deferred_bf16(gt_tree *t, cudaStream_t s);
+
+void launch_drain(gt_tree *t, int fmt, int cut, const SibPair *root, const uint32_t *root_count,
+                  cudaStream_t s, uint32_t *level_count, uint32_t *left_count) {
+  Workspace &w = t->ws;
+  LevelArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.expire = t->expire_waits;
+  const int eb = entry_bytes(fmt);
+  a.rows = fmt == GT_F32 ? reinterpret_cast<const uint8_t *>(t->rows32)
+           : fmt == GT_BF16 ? reinterpret_cast<const uint8_t *>(t->rows16)
+                            : t->rows8;
+  a.scales = fmt == GT_FP8 ? t->scale8 : nullptr;
+  a.row_bytes = t->stride * eb;
+  a.nvec = (int)((t->d * eb + 15) / 16);
+  a.qf32 = w.qf32;
+  a.qstride = t->stride;
+  a.qn1 = w.qn1;
+  a.rho = w.rho;
+  a.res = w.res;
+  a.res_count = w.counters + kMaxLevels;
+  a.res_cap = (uint32_t)std::min<int64_t>(w.res_cap, 0xffffffffLL);
+  a.rchk = w.rchk;
+  a.rchk_count = w.counters + kMaxLevels + 1;
+  a.rchk_cap = (uint32_t)w.rchk_cap;
+  a.flags = t->flags;
+  a.q_lim = (uint32_t)w.q_cap;
+  a.rows32 = t->rows32;
+  a.bd32 = make_bound(GT_F32, 0, t->d);
+  a.rows16 = t->rows16;
+  a.bd16 = make_bound(GT_BF16, 0, t->d);
+  a.refine_count = w.counters + kMaxLevels + 2;
+  const bool defer = defer_active(t, fmt);
+  if (defer) {
+    cudaMemsetAsync(w.counters + kDeferSlot, 0, sizeof(uint32_t), s);
+    a.defer = w.defer;
+    a.defer_count = w.counters + kDeferSlot;
+    a.defer_cap = (uint32_t)w.defer_cap;
+  }
+  DrainArgs g;
+  std::memset(&g, 0, sizeof(g));
+  for (int h = 0; h < cut; ++h) {
+    g.lvl[h].row0 = t->lvl_off[h];
+    g.lvl[h].n_rows = (uint32_t)level_rows(t->N, h);
+    g.lvl[h].bd = make_bound(fmt, bound_level(t, h), t->d);
+  }
+  g.root = root;
+  g.root_count = root_count;
+  g.root_cap = (uint32_t)(w.front_lim / 2);  // SibPairs are two Pairs wide
+  g.head = w.counters + kDrainHeadSlot;
+  g.level_count = level_count ? level_count : w.counters;
+  g.left_count = left_count ? left_count : w.counters + kLeftItemsSlot;
+  g.scratch = reinterpret_cast<SibPair *>(w.drain);
+  g.wcap = 32u << (cut - 1);
+  g.cut = cut;
+  cudaMemsetAsync(g.head, 0, sizeof(uint32_t), s);
+  const bool wide = kv_for<GT_F32>(t->d) != 1024 / (32 * 4);
+  if (fmt == GT_BF16)
+    wide ? launch_drain_t<GT_BF16, 8>(a, g, t->sm_count, s) : launch_drain_t<GT_BF16, 4>(a, g, t->sm_count, s);
+  else if (fmt == GT_FP8)
+    wide ? launch_drain_t<GT_FP8, 4>(a, g, t->sm_count, s) : launch_drain_t<GT_FP8, 2>(a, g, t->sm_count, s);
+  else
+    wide ? launch_drain_t<GT_F32, 16>(a, g, t->sm_count, s) : launch_drain_t<GT_F32, 8>(a, g, t->sm_count, s);
+  if (defer) launch_deferred_bf16(t, s);
 }
 
 bool launch_prefix(gt_tree *t, int fmt, int h, const SibPair *in, const uint32_t *in_count,

@@ -64,20 +64,24 @@ class AutotuneResult(ctypes.Structure):
     _fields_ = [("cutover", _c_i32), ("inflight", _c_i32), ("tile_n", _c_i32),
                 ("best_ms", ctypes.c_float), ("ms_cutover", ctypes.c_float * 9),
                 ("ms_cutover_sub", ctypes.c_float * 9),
-                ("ms_inflight", ctypes.c_float * 7), ("ms_tile", ctypes.c_float * 4),
+                ("ms_inflight", ctypes.c_float * 8), ("ms_tile", ctypes.c_float * 4),
                 ("subtract", _c_i32)]
+
+
+SCHEDULES = {"auto": 0, "levels": 1, "drain": 2}
 
 
 class ServerOpts(ctypes.Structure):
     _fields_ = [("stream", _c_p), ("dtype", _c_i32), ("cutover", _c_i32),
-                ("max_group", _c_i64), ("scratch_bytes", _c_i64), ("queue_capacity", _c_i64)]
+                ("max_group", _c_i64), ("scratch_bytes", _c_i64), ("queue_capacity", _c_i64),
+                ("schedule", _c_i32), ("reserved", _c_i32)]
 
 
 class ServerStats(ctypes.Structure):
     _fields_ = [(k, _c_i64) for k in ("submitted", "admitted", "completed", "pending",
                                       "inserted", "steps", "launches", "retries", "rechecks",
                                       "refines", "gathered_tests", "dense_tests", "cutover",
-                                      "max_group")] + [("busy_seconds", _c_f64)]
+                                      "max_group", "schedule")] + [("busy_seconds", _c_f64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -434,7 +438,7 @@ class Tree:
         ms.update({f"cutover{c}_sub": float(r.ms_cutover_sub[c]) for c in range(2, 9)
                    if r.ms_cutover_sub[c] > 0})
         ms.update({f"inflight{g}": float(r.ms_inflight[i])
-                   for i, g in enumerate((1, 2, 4, 9, 10, 12, 16)) if r.ms_inflight[i] > 0})
+                   for i, g in enumerate((1, 2, 4, 9, 10, 12, 16, 32)) if r.ms_inflight[i] > 0})
         ms.update({f"tile{n}": float(r.ms_tile[i]) for i, n in enumerate((128, 256, 512, 1024))
                    if r.ms_tile[i] > 0})
         return {"cutover": r.cutover, "inflight": r.inflight, "tile_n": r.tile_n,
@@ -507,8 +511,10 @@ class Server:
     (tag, ids, n_snapshot) tuples."""
 
     def __init__(self, tree: Tree, dtype="bf16", cutover: int = -1, max_group: int = 0,
-                 scratch_bytes: int = 0, queue_capacity: int = 0, stream=None):
+                 scratch_bytes: int = 0, queue_capacity: int = 0, stream=None,
+                 schedule: str = "auto"):
         o = ServerOpts()
+        o.schedule = SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule)
         o.stream = _stream_ptr(stream)
         o.dtype = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
         o.cutover = cutover

@@ -158,9 +158,9 @@ def test_prefix_refusals(gt, small_ds):
     with pytest.raises(gt.GTError):
         t.exhaustive(Q, rho)
     with pytest.raises(gt.GTError):
-        t.autotune(Q, rho)
+        gt.Server(t, cutover=4)                       # its dense level is prefix_level
     with pytest.raises(gt.GTError):
-        gt.Server(t)
+        t.set_tuning("bf16", inflight=2)              # splits always use the ring
     with pytest.raises(gt.GTError):
         t.pair_bounds(0, "bf16", Q, np.zeros((1, 2), dtype=np.int32))
     with pytest.raises(gt.GTError):
@@ -173,4 +173,23 @@ def test_prefix_refusals(gt, small_ds):
         t.query_static(Qd, rd, off, ids)
     # the tree stays usable after the refusals
     same_sets(t.query(Q, rho, dtype="bf16"), oracle.brute_force(F, Q, rho))
+    t.close()
+
+
+def test_prefix_autotune_picks_a_tile(gt, small_ds):
+    ds = small_ds
+    F = ds.F[:12_000]
+    rho = ds.rho_for(0.9)
+    ref = oracle.brute_force(F, ds.Q, rho)
+    assert ref.ambiguous.sum() == 0
+    t = gt.Tree(F, layout="prefix", prefix_level=3)
+    tune = t.autotune(ds.Q, rho)
+    assert tune["cutover"] == 3 and tune["subtract"] == 0
+    assert tune["tile_n"] in (128, 256, 512, 1024)
+    assert abs(tune["best_ms"] - min(v for k, v in tune["ms"].items() if k.startswith("tile"))) < 1e-6
+    res = t.query(ds.Q, rho, dtype="bf16")
+    same_sets(res, ref)
+    for tile in (128, 512, 1024):
+        t.set_tuning("bf16", tile=tile)
+        same_sets(t.query(ds.Q, rho, dtype="bf16"), ref)
     t.close()

@@ -25,8 +25,8 @@ def stream_ds():
     return synth.generate("softmax_n1m_d512_served", n_queries=700, N=43_000)
 
 
-def _serve(gt, t, ds, n0, dtype, max_group, insert_every):
-    srv = gt.Server(t, dtype=dtype, max_group=max_group)
+def _serve(gt, t, ds, n0, dtype, max_group, insert_every, schedule="auto"):
+    srv = gt.Server(t, dtype=dtype, max_group=max_group, schedule=schedule)
     B = ds.Q.shape[0]
     rng = np.random.default_rng(3)
     arrivals = np.sort(rng.integers(0, 40, B))          # step at which each query arrives
@@ -52,10 +52,12 @@ def _serve(gt, t, ds, n0, dtype, max_group, insert_every):
 
 @pytest.mark.parametrize("dtype", ["bf16", "fp8"])
 def test_served_results_exact_with_inserts(gt, stream_ds, dtype):
+    # one level per step: several groups in flight at different levels
     ds = stream_ds
     n0 = 40_000
     t = gt.Tree(ds.F[:n0], capacity=ds.F.shape[0])
-    done, st = _serve(gt, t, ds, n0, dtype, max_group=64, insert_every=3)
+    done, st = _serve(gt, t, ds, n0, dtype, max_group=64, insert_every=3, schedule="levels")
+    assert st["schedule"] == 1
     assert st["completed"] == ds.Q.shape[0] and st["inserted"] == ds.F.shape[0] - n0
     assert st["steps"] > st["completed"] / 64                # several groups in flight
     by_snap = {}
@@ -68,6 +70,90 @@ def test_served_results_exact_with_inserts(gt, stream_ds, dtype):
         assert ref.ambiguous.sum() == 0
         for i, tag in enumerate(tags):
             assert np.array_equal(done[tag][0], ref.neighbours(i)), f"query {tag} (N={snap})"
+    t.close()
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f32"])
+def test_prefix_served_results_exact_with_inserts(gt, stream_ds, dtype):
+    # the prefix layout (Eq. 1's cumulative sums restarted per block of 8
+    # items) behind the same server: GEMM over the blocks' totals, one prefix
+    # split per kept pool and step; inserts append items and extend the last
+    # block, which leaves every prefix row a group admitted earlier reads as it was
+    ds = stream_ds
+    n0 = 40_000
+    t = gt.Tree(ds.F[:n0], capacity=41_000, layout="prefix", prefix_level=3,
+                formats=("bf16", "f32"))
+    done, st = _serve(gt, t, ds, n0, dtype, max_group=64, insert_every=3)
+    assert t.size == ds.F.shape[0]                           # grown past the capacity
+    assert st["completed"] == ds.Q.shape[0] and st["cutover"] == 3
+    by_snap = {}
+    for tag, (ids, snap) in done.items():
+        by_snap.setdefault(snap, []).append(tag)
+    assert len(by_snap) >= 3
+    for snap, tags in by_snap.items():
+        tags = np.array(sorted(tags))
+        ref = oracle.brute_force(ds.F[:snap], ds.Q[tags], ds.rho[tags])
+        assert ref.ambiguous.sum() == 0
+        for i, tag in enumerate(tags):
+            assert np.array_equal(done[tag][0], ref.neighbours(i)), f"query {tag} (N={snap})"
+    t.close()
+
+
+def test_prefix_served_equals_alone(gt, stream_ds):
+    ds = stream_ds
+    n0 = 40_000
+    t = gt.Tree(ds.F[:n0], capacity=ds.F.shape[0], layout="prefix", prefix_level=3)
+    done, _ = _serve(gt, t, ds, n0, "bf16", max_group=128, insert_every=5)
+    t.close()
+    rng = np.random.default_rng(11)
+    for tag in rng.choice(ds.Q.shape[0], 12, replace=False):
+        ids, snap = done[int(tag)]
+        alone = gt.Tree(ds.F[:snap], layout="prefix", prefix_level=3)
+        res = alone.query(ds.Q[tag:tag + 1], ds.rho[tag:tag + 1], dtype="bf16")
+        assert np.array_equal(res.neighbours(0), ids)
+        alone.close()
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "fp8"])
+def test_drain_server_exact_with_inserts(gt, stream_ds, dtype):
+    # tests in flight code 32: each step drains the group admitted the step
+    # before (every level below the cutover and its items in one launch)
+    # while it admits the next
+    ds = stream_ds
+    n0 = 40_000
+    t = gt.Tree(ds.F[:n0], capacity=ds.F.shape[0])
+    done, st = _serve(gt, t, ds, n0, dtype, max_group=64, insert_every=3, schedule="drain")
+    assert st["schedule"] == 2
+    assert st["completed"] == ds.Q.shape[0] and st["inserted"] == ds.F.shape[0] - n0
+    by_snap = {}
+    for tag, (ids, snap) in done.items():
+        by_snap.setdefault(snap, []).append(tag)
+    assert len(by_snap) >= 3
+    for snap, tags in by_snap.items():
+        tags = np.array(sorted(tags))
+        ref = oracle.brute_force(ds.F[:snap], ds.Q[tags], ds.rho[tags])
+        assert ref.ambiguous.sum() == 0
+        for i, tag in enumerate(tags):
+            assert np.array_equal(done[tag][0], ref.neighbours(i)), f"query {tag} (N={snap})"
+    # the same tests as the level-by-level server (one group at a time)
+    srv_counts = {}
+    for code in ("levels", "drain"):
+        srv = gt.Server(t, dtype=dtype, max_group=4096, schedule=code)
+        srv.submit(ds.Q, ds.rho, np.arange(ds.Q.shape[0]))
+        got = {}
+        for _ in range(100):
+            srv.step()
+            for tag, ids, snap in srv.poll():
+                got[tag] = ids
+            if len(got) == ds.Q.shape[0]:
+                break
+        srv_counts[code] = srv.stats()
+        srv.close()
+        ref = oracle.brute_force(ds.F, ds.Q, ds.rho)
+        for tag in range(ds.Q.shape[0]):
+            assert np.array_equal(got[tag], ref.neighbours(tag))
+    assert srv_counts["drain"]["gathered_tests"] == srv_counts["levels"]["gathered_tests"]
+    assert srv_counts["drain"]["steps"] < srv_counts["levels"]["steps"]
     t.close()
 
 
@@ -89,7 +175,7 @@ def test_insert_into_a_tail_sibling_keeps_the_left_bound(gt):
     ref = oracle.brute_force(F[:n0], q, rho, margin=0.0)
     assert 3996 in ref.neighbours(0)
     t = gt.Tree(F[:n0], capacity=n0 + 16)
-    srv = gt.Server(t, dtype="bf16", cutover=3)
+    srv = gt.Server(t, dtype="bf16", cutover=3, schedule="levels")
     srv.submit(q, rho, np.array([7]))
     srv.step()                           # admitted: the level-3 GEMM
     srv.step()                           # level 2: right children tested, left ones bounded
@@ -110,7 +196,8 @@ def test_served_equals_alone(gt, stream_ds):
     ds = stream_ds
     n0 = 40_000
     t = gt.Tree(ds.F[:n0], capacity=ds.F.shape[0])
-    done, _ = _serve(gt, t, ds, n0, "bf16", max_group=128, insert_every=5)
+    done, st = _serve(gt, t, ds, n0, "bf16", max_group=128, insert_every=5)
+    assert st["schedule"] == 2                               # the automatic choice here
     t.close()
     rng = np.random.default_rng(9)
     for tag in rng.choice(ds.Q.shape[0], 12, replace=False):
@@ -137,7 +224,7 @@ def test_server_admission_backs_off_on_overflow(gt, stream_ds):
     t = gt.Tree(ds.F)
     # a frontier budget far below one full group's survivors: groups are cut
     # until they fit, and every answer is still exact
-    srv = gt.Server(t, dtype="bf16", max_group=512, scratch_bytes=1 << 21)
+    srv = gt.Server(t, dtype="bf16", max_group=512, scratch_bytes=1 << 21, schedule="levels")
     srv.submit(ds.Q, ds.rho, np.arange(ds.Q.shape[0]))
     done = {}
     for _ in range(5000):

@@ -203,7 +203,7 @@ def test_autotune_choice_is_used_and_exact(gt, small_ds):
     t = gt.Tree(ds.F)
     for dtype in ("bf16", "fp8"):
         tune = t.autotune(ds.Q, r, dtype=dtype)
-        assert 1 <= tune["cutover"] <= min(8, t.levels - 1) and tune["inflight"] in (0, 1, 2, 4, 9, 10, 12, 16)
+        assert 1 <= tune["cutover"] <= min(8, t.levels - 1) and tune["inflight"] in (0, 1, 2, 4, 9, 10, 12, 16, 32)
         assert tune["tile_n"] in (128, 256, 512, 1024)
         assert abs(tune["best_ms"] - min(tune["ms"].values())) < 1e-6
         res = t.query(ds.Q, r, dtype=dtype)               # automatic cutover = tuned

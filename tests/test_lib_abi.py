@@ -42,4 +42,7 @@ def test_struct_layouts_match_header():
     assert gt.QueryStats.level_tests.offset == 7 * 8 + 2 * 4
     assert gt.QueryStats.launches.offset == 7 * 8 + 2 * 4 + 64 * 8 + 8
     assert ctypes.sizeof(gt.QueryStats) == 7 * 8 + 2 * 4 + 64 * 8 + 8 + 2 * 8 + 8 * 4 + 3 * 8
-    assert ctypes.sizeof(gt.AutotuneResult) == 4 * (3 + 1 + 9 + 9 + 7 + 4 + 1)
+    assert ctypes.sizeof(gt.AutotuneResult) == 4 * (3 + 1 + 9 + 9 + 8 + 4 + 1)
+    assert ctypes.sizeof(gt.ServerOpts) == 8 + 4 + 4 + 8 + 8 + 8 + 4 + 4
+    assert gt.ServerOpts.schedule.offset == 40
+    assert ctypes.sizeof(gt.ServerStats) == 16 * 8
