@@ -224,7 +224,7 @@ def _dist():
 
 
 def serve_run(gt, tree, Q, rhos, rate, n_req, dtype, inserts=None, insert_frac=0.01, seed=0,
-              schedule="auto"):
+              schedule="auto", rho_per_query=None):
     """Poisson request stream through the continuous-batching server.
 
     Returns achieved queries/s (completed / span from first arrival to last
@@ -237,7 +237,8 @@ def serve_run(gt, tree, Q, rhos, rate, n_req, dtype, inserts=None, insert_frac=0
         arrivals = np.zeros(n_req)
     qi = rng.integers(0, B, n_req)
     Qreq = np.ascontiguousarray(Q[qi])   # the requests' vectors, made before the clock starts
-    rho = rhos[rng.integers(0, len(rhos), n_req)].astype(np.float32)
+    rho = (rho_per_query[qi] if rho_per_query is not None
+           else rhos[rng.integers(0, len(rhos), n_req)]).astype(np.float32)
     is_ins = rng.random(n_req) < insert_frac if inserts is not None else np.zeros(n_req, bool)
     srv = gt.Server(tree, dtype=dtype, queue_capacity=n_req, schedule=schedule)
     lat = np.full(n_req, np.nan)
@@ -282,6 +283,164 @@ def serve_run(gt, tree, Q, rhos, rate, n_req, dtype, inserts=None, insert_frac=0
             "cutover": st["cutover"], "launches": st["launches"],
             "schedule": {1: "levels", 2: "drain"}.get(st["schedule"], st["schedule"])}
 
+
+
+def side_by_side(gt, tree, Fd, Qd, rd, B, dtype, tune, flush, capacity, reps=3):
+    """The batch split in two halves answered at the same time by two trees
+    over the same rows, each call's kernels sized for part of the SMs
+    (gt_set_sm_limit) and issued from its own host thread and stream, so one
+    half's dense GEMM (tensor-bound) can overlap the other's gathers
+    (memory-bound).  Host wall-clock seconds per batch, against the same
+    batch in one call on every SM, timed the same way."""
+    import threading
+    import torch
+    sub = 1 if tune.get("subtract") else -1
+    kw = dict(dtype=dtype, cutover=tune["cutover"], subtract=sub, results_on_device=True)
+    tree2 = gt.Tree(Fd, capacity=capacity)
+    tree2.set_tuning(dtype, cutover=tune["cutover"], inflight=tune["inflight"], tile=tune["tile_n"])
+    trees = (tree, tree2)
+    streams = (torch.cuda.Stream(), torch.cuda.Stream())
+    halves = ((0, B // 2), (B // 2, B))
+
+    def wall(fn):
+        best = None
+        for rep in range(reps + 1):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            if rep > 0:
+                best = dt if best is None else min(best, dt)
+        return best
+
+    def one_call():
+        tree.query(Qd, rd, stream=streams[0], **kw).free()
+
+    def two_calls():
+        res = [None, None]
+
+        def run(i):
+            lo, hi = halves[i]
+            res[i] = trees[i].query(Qd[lo:hi], rd[lo:hi], stream=streams[i], **kw)
+        ths = [threading.Thread(target=run, args=(i,)) for i in (0, 1)]
+        for th in ths:
+            th.start()
+        for th in ths:
+            th.join()
+        for r in res:
+            r.free()
+
+    out = {"call": "gt_query, two trees, two host threads and streams, halves of the batch",
+           "one_call_all_sms_ms": round(1e3 * wall(one_call), 3)}
+    n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    for split in (n_sm * 5 // 12, n_sm // 2, n_sm * 7 // 12):
+        tree.set_sm_limit(split)
+        tree2.set_sm_limit(n_sm - split)
+        out[f"two_calls_{split}_{n_sm - split}_sms_ms"] = round(1e3 * wall(two_calls), 3)
+    tree.set_sm_limit(0)
+    tree2.close()
+    best = min(v for k, v in out.items() if k.startswith("two_calls"))
+    out["speedup_best_split"] = round(out["one_call_all_sms_ms"] / best, 3)
+    return out
+
+
+def served_d512_run(gt, flush, rates=(5000.0, 20000.0, 50000.0)):
+    """The served form at N = 1M, d = 512: BF16 rows, per-query rho ~ U[0.8,
+    0.97], 1% of requests inserts; the batch path's queries/s (CUDA events)
+    and the server's p50/p99 at the offered rates."""
+    import torch
+    import synth
+    ds = synth.generate("softmax_n1m_d512_served")
+    B = ds.Q.shape[0]
+    Fd = torch.from_numpy(ds.F).cuda()
+    t = gt.Tree(Fd, capacity=ds.F.shape[0] + 65536)
+    del Fd
+    Qd, rd = torch.from_numpy(ds.Q).cuda(), torch.from_numpy(ds.rho).cuda()
+    stream = torch.cuda.current_stream()
+    tune = t.autotune(Qd, rd, dtype="bf16", stream=stream)
+    t.query(Qd, rd, results_on_device=True, stream=stream).free()
+    ts = []
+    for _ in range(3):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = t.query(Qd, rd, results_on_device=True, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+        r.free()
+    extra = ds.F[np.random.default_rng(9).choice(ds.F.shape[0], 4096, replace=False)]
+    served = [serve_run(gt, t, ds.Q, None, r_, int(min(20000, max(8000, r_ * 0.4))), "bf16",
+                        inserts=extra, seed=13, rho_per_query=ds.rho) for r_ in rates]
+    t.close()
+    return {"workload": "softmax_n1m_d512_served", "N": int(ds.F.shape[0]), "d": int(ds.F.shape[1]),
+            "queries": int(B), "rho": "per query, U[0.8, 0.97]",
+            "batch_qps": round(B / (statistics.mean(ts) / 1e3), 1), "unit": UNIT,
+            "autotune": {k: tune[k] for k in ("cutover", "inflight", "tile_n", "subtract")},
+            "serving": served}
+
+
+def signed_run(gt, flush, check, N=262144, d=256, B=2000, rho=0.8, n_check=64):
+    """Descriptors with negative entries (Sec. 2: pools by element-wise
+    maximum and minimum; the paper runs no experiment on them): seeded
+    Gaussian unit vectors, queries a random item plus noise (cosine about
+    0.94 to it), a GT_POOL_MAXMIN tree, autotuned.  Queries/s with inputs on
+    the device, CUDA events; beside it a dense FP32 library product (cuBLAS
+    through torch) with the threshold applied, for context; the sets checked
+    against the oracle's FP64 brute force on a sample of the queries."""
+    import torch
+    import synth
+    F, Q = synth.signed_workload(N, d, B, noise=0.35 / np.sqrt(d), seed=11)
+    Fd, Qd = torch.from_numpy(F).cuda(), torch.from_numpy(Q).cuda()
+    rd = torch.full((B,), rho, dtype=torch.float32, device="cuda")
+    t = gt.Tree(Fd, pooling="maxmin")
+    tune = t.autotune(Qd, rd, dtype="bf16")
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, n=3):
+        warm = fn()
+        if hasattr(warm, "free"):
+            warm.free()
+        ts, stats = [], None
+        for _ in range(n):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+            if hasattr(r, "free"):
+                stats = r.stats
+                r.free()
+        return B / (statistics.mean(ts) / 1e3), stats
+    qps, st = timed(lambda: t.query(Qd, rd, dtype="bf16", results_on_device=True, stream=stream))
+
+    def library():
+        hits = 0
+        for lo in range(0, N, 65536):
+            hits += int((Qd @ Fd[lo:lo + 65536].T >= rho).sum())
+        return hits
+    torch.backends.cuda.matmul.allow_tf32 = False
+    lib_qps, _ = timed(library)
+    out = {"workload": f"signed Gaussian unit vectors, N={N}, d={d}, {B} queries, rho={rho}",
+           "value": round(qps, 1), "unit": "queries/s", "cutover": tune["cutover"],
+           "inflight": tune["inflight"], "tests_per_query": st["tests"] / B,
+           "gathered_tests_per_query": st["gathered_tests"] / B,
+           "rechecks_per_query": st["rechecks"] / B, "results_per_query": st["results"] / B,
+           "fp32_library_product_qps": round(lib_qps, 1)}
+    if check:
+        import oracle
+        res = t.query(Q[:n_check], np.full(n_check, rho, np.float32), dtype="bf16")
+        ref = oracle.brute_force(F, Q[:n_check], np.full(n_check, rho, np.float32))
+        out["parity_sample"] = {"queries": n_check, "oracle": "brute_force (FP64)",
+                                "identical": bool(np.array_equal(res.offsets, ref.offsets)
+                                                  and np.array_equal(res.ids, ref.ids)),
+                                "oracle_ambiguous": int(ref.ambiguous.sum())}
+    t.close()
+    return out
 
 
 def streaming_run(gt, ds, dtype, rho, chunk=100, n_check=256, seed=0):
@@ -608,6 +767,24 @@ def main():
             comparators[name] = {"value": round(qps, 1), "unit": UNIT,
                                  "tests_per_query": s["tests"] / B,
                                  "gathered_bytes_per_query": s["gathered_bytes"] / B}
+        if a.dtype != "fp8" and tune is not None:
+            # FP8 rows at the same cutover: where the extra time goes (tests per
+            # level, leaf re-scores from the BF16 and FP32 rows, FP64 rechecks)
+            qps, s = timed(lambda: tree.query(Qd, rd, dtype="fp8", results_on_device=True,
+                                              stream=stream, timing=True))
+            comparators["fp8_rows"] = {
+                "value": round(qps, 1), "unit": UNIT, "cutover": s["cutover"],
+                "gathered_tests_per_query": s["gathered_tests"] / B,
+                "level_tests_per_query": [round(x / B, 1) for x in
+                                          s["level_tests"][:max(0, s["cutover"]) + 1]],
+                "refines_per_query": s["refines"] / B, "rechecks_per_query": s["rechecks"] / B,
+                "gathered_bytes_per_query": s["gathered_bytes"] / B, "kernel_ms": s["kernel_ms"],
+                "bf16_rows": {"gathered_tests_per_query": st0["gathered_tests"] / B,
+                              "level_tests_per_query": [round(x / B, 1) for x in
+                                                        st0["level_tests"][:max(0, st0["cutover"]) + 1]],
+                              "refines_per_query": st0["refines"] / B,
+                              "rechecks_per_query": st0["rechecks"] / B,
+                              "gathered_bytes_per_query": st0["gathered_bytes"] / B}}
         for c in [int(x) for x in a.sweep_cutover.split(",") if x.strip()]:
             qps, s = timed(lambda: tree.query(Qd, rd, dtype=a.dtype, cutover=c,
                                               results_on_device=True, stream=stream, timing=True))
@@ -644,6 +821,12 @@ def main():
         mres.free()
         ref_res.free()
         mtree.close()
+        torch.cuda.empty_cache()
+        if tune is not None:
+            comparators["side_by_side"] = side_by_side(gt, tree, Fd, Qd, rd, B, a.dtype, tune, flush,
+                                                       N + 65536)
+            torch.cuda.empty_cache()
+        comparators["signed_maxmin"] = signed_run(gt, flush, rank == 0 and not a.no_cpu)
         torch.cuda.empty_cache()
         # the paper's prefix-sum layout (Eq. 1), with the sums restarted per
         # block of 2^3 items: N prefix rows instead of a row per pool
@@ -747,6 +930,10 @@ def main():
     # the paper's streaming setting, on a tree of its own (after the main tree is freed)
     tree.close()
     tree = None
+    served_d512 = None
+    if not a.no_serve and not pre and rank == 0 and a.workload == "softmax_n1m_d1000":
+        torch.cuda.empty_cache()
+        served_d512 = served_d512_run(gt, flush)
     streaming = None
     if not a.no_stream and rank == 0:
         streaming = streaming_run(gt, ds, a.dtype, 0.9 if 0.9 in (ds.workload.rhos or ()) else a.rho)
@@ -789,6 +976,7 @@ def main():
                                "micro_batches": st0["micro_batches"], "kernel_ms": km},
             "comparators": comparators,
             "serving": serving,
+            "served_n1m_d512": served_d512,
             "streaming": streaming,
             "parity_sample": parity,
             "build_s": round(build_s, 3), "generate_s": round(t_gen, 1),

@@ -471,6 +471,13 @@ gt_status gt_server_poll(gt_server *s, int64_t max_queries, int64_t *n_done, int
 gt_status gt_server_get_stats(const gt_server *s, gt_server_stats *out);
 void gt_server_free(gt_server *s);
 
+/* Run the kernels of later calls on tree t (queries, the server's steps,
+ * inserts) on grids sized for at most n SMs (n <= 0: all of the device's), so
+ * that calls on several trees and streams can share the GPU side by side:
+ * the persistent kernels (one block per SM) then leave the other SMs to the
+ * other calls' kernels.  n >= 2.  The paper has no counterpart. */
+gt_status gt_set_sm_limit(gt_tree *t, int32_t n);
+
 /* Failure detection (the bounded device waits): every wait of the gather
  * kernels on their bulk copies gives up after 1 s, raises a status word that
  * the call reads, and the call returns GT_ETIMEOUT with no results instead of

@@ -246,6 +246,7 @@ gt_status scan_context(int dev, int64_t N, int32_t d, gt_tree **out) {
     x->formats = (1u << GT_F32) | (1u << GT_BF16);
     x->device = dev;
     cudaDeviceGetAttribute(&x->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    x->sm_total = x->sm_count;
     cudaError_t e = cudaMalloc(&x->flags, 64 * sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(x->flags, 0, 64 * sizeof(int));
     if (e != cudaSuccess || x->sm_count <= 0) {
@@ -333,6 +334,7 @@ gt_status gt_build(const float *F, int64_t N, int32_t d, const gt_build_opts *op
   cudaGetDevice(&dev);
   t->device = dev;
   cudaDeviceGetAttribute(&t->sm_count, cudaDevAttrMultiProcessorCount, dev);
+  t->sm_total = t->sm_count;
   if (t->sm_count <= 0) {
     delete t;
     return set_error(GT_ECUDA, "no CUDA device");
@@ -737,7 +739,7 @@ static gt_status run_search_on(gt_tree *t, const float *Q, int64_t B, const floa
     GraphKey key;
     std::memset(&key, 0, sizeof(key));
     key.cut = cut; key.fmt = fmt; key.timing = tm.on ? 1 : 0;
-    key.pad = (sub ? 1 : 0) | (t->expire_waits ? 2 : 0);
+    key.pad = (sub ? 1 : 0) | (t->expire_waits ? 2 : 0) | (t->sm_count << 8);
     key.tuned_g = t->tuned_g[fmt]; key.tuned_bn = t->tuned_bn;
     key.q0 = q0; key.b = b; key.N = t->N; key.front_lim = w.front_lim;
     key.res_cap = w.res_cap; key.rchk_cap = w.rchk_cap;
@@ -1302,6 +1304,13 @@ gt_status gt_read_rows(const gt_tree *t, int32_t level, int32_t dtype, int64_t f
                        (size_t)t->d * eb, (size_t)count, cudaMemcpyDeviceToHost));
   if (scales_out && dtype == GT_FP8)
     GT_CUDA(cudaMemcpy(scales_out, t->scale8 + row0, (size_t)count * 4, cudaMemcpyDeviceToHost));
+  return GT_OK;
+}
+
+gt_status gt_set_sm_limit(gt_tree *t, int32_t n) {
+  if (!t) return set_error(GT_EINVAL, "null tree");
+  if (n > 0 && n < 2) return set_error(GT_EINVAL, "an SM limit must be at least 2");
+  t->sm_count = n > 0 ? std::min(n, t->sm_total) : t->sm_total;
   return GT_OK;
 }
 

@@ -995,7 +995,9 @@ gt_status launch_dense_impl(gt_tree *t, int h, int mode, int64_t q0, int64_t b, 
   }
   const int bmc = (shape == 2 || shape == 3) ? 256 : 128, bn = shape == 1 ? 128 : 256;
   const int64_t tiles = ((b + bmc - 1) / bmc) * ((rows + bn - 1) / bn);
-  const int grid = shape == 3 ? 2 * (int)std::max<int64_t>(1, std::min<int64_t>(tiles, pair_clusters()))
+  const int grid = shape == 3 ? 2 * (int)std::max<int64_t>(
+                                      1, std::min<int64_t>({tiles, (int64_t)pair_clusters(),
+                                                            (int64_t)t->sm_count / 2}))
                               : (int)std::max<int64_t>(1, std::min<int64_t>(tiles, t->sm_count));
   auto go = [&](auto kern, int threads, int smem) -> gt_status {
     static bool attr[4] = {false, false, false, false};

@@ -163,7 +163,8 @@ struct gt_tree {
   int *flags = nullptr;          // device status words
   float max_norm_dev = 0.f;      // max | ||f||_2 - 1 | seen at build / insert
   cudaStream_t stream = nullptr;
-  int sm_count = 0;
+  int sm_count = 0;              // SMs the tree's kernels size their grids for
+  int sm_total = 0;              // SMs of the device (gt_set_sm_limit restores it)
   int device = 0;                // CUDA device the tree's memory lives on
   int tuned_cut[3] = {0, 0, 0};  // cutover level chosen by gt_autotune, per row format
   int tuned_g[3] = {0, 0, 0};    // tests in flight per warp chosen by gt_autotune

@@ -99,6 +99,7 @@ ENTRY_POINTS = ("gt_build", "gt_insert", "gt_query", "gt_query_into", "gt_exhaus
                 "gt_dense_scores", "gt_pair_bounds", "gt_query_static", "gt_server_create", "gt_server_submit",
                 "gt_server_insert", "gt_server_step", "gt_server_poll", "gt_server_get_stats",
                 "gt_server_free", "gt_autotune", "gt_set_tuning", "gt_set_wait_expiry",
+                "gt_set_sm_limit",
                 "gt_size", "gt_dim", "gt_levels", "gt_free", "gt_csr_free", "gt_last_error")
 
 
@@ -147,6 +148,8 @@ def load(build_if_missing: bool = True):
     lib.gt_set_tuning.restype = _c_i32
     lib.gt_set_wait_expiry.argtypes = [P, _c_i32]
     lib.gt_set_wait_expiry.restype = _c_i32
+    lib.gt_set_sm_limit.argtypes = [P, _c_i32]
+    lib.gt_set_sm_limit.restype = _c_i32
     lib.gt_server_free.argtypes = [P]
     lib.gt_server_free.restype = None
     for f in ("gt_build", "gt_insert", "gt_query", "gt_exhaustive", "gt_exhaustive_tree",
@@ -448,6 +451,11 @@ class Tree:
         """gt_set_tuning: pin the cutover level, tests in flight, GEMM tile."""
         _check(load().gt_set_tuning(self._h, DTYPES[dtype] if isinstance(dtype, str) else dtype,
                                     cutover, inflight, tile))
+
+    def set_sm_limit(self, n: int):
+        """gt_set_sm_limit: size later calls' grids for at most n SMs (0: all),
+        so that calls on several trees and streams share the GPU."""
+        _check(load().gt_set_sm_limit(self._h, int(n)))
 
     def set_wait_expiry(self, on: bool):
         """gt_set_wait_expiry: make the gather kernels' first bounded wait run

@@ -458,3 +458,38 @@ def test_query_into_caller_buffers(gt, small_ds):
     with pytest.raises(TypeError):
         t.query_into(ds.Q, rho, np.empty(B + 1, np.int32), np.empty(n_ref, np.int32))
     t.close()
+
+
+def test_sm_limit_side_by_side_calls(gt, small_ds):
+    # two trees whose calls run on about half of the SMs each, from two host
+    # threads on two streams: both answers exact
+    import threading
+    ds = small_ds
+    r = ds.rho_for(0.9)
+    ref = oracle.brute_force(ds.F, ds.Q, r)
+    trees = [gt.Tree(ds.F), gt.Tree(ds.F)]
+    for t_, n in zip(trees, (40, 112)):
+        t_.set_sm_limit(n)
+        t_.set_tuning("bf16", inflight=16)
+    Qd = torch.from_numpy(ds.Q).cuda()
+    rd = torch.from_numpy(r).cuda()
+    out = [None, None]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+
+    def run(i):
+        out[i] = trees[i].query(Qd, rd, dtype="bf16", cutover=3, subtract=1, stream=streams[i])
+
+    for _ in range(2):
+        ths = [threading.Thread(target=run, args=(i,)) for i in (0, 1)]
+        for th in ths:
+            th.start()
+        for th in ths:
+            th.join()
+        for res in out:
+            same_sets(res, ref)
+    trees[0].set_sm_limit(0)                      # all SMs again
+    same_sets(trees[0].query(ds.Q, r, dtype="bf16", cutover=3, subtract=1), ref)
+    with pytest.raises(gt.GTError):
+        trees[0].set_sm_limit(1)
+    for t_ in trees:
+        t_.close()
