@@ -74,6 +74,8 @@ def _args():
     p.add_argument("--no-stream", action="store_true", help="skip the streaming-setting run")
     p.add_argument("--no-e2e", action="store_true",
                    help="skip the end-to-end calls (small profiling runs)")
+    p.add_argument("--no-large", action="store_true",
+                   help="skip the large form (N = 10M, FP8 rows, 100,000 queries)")
     p.add_argument("--serve-rates", default="50000,400000,0",
                    help="offered request rates for the serving run (0: all at once)")
     return p.parse_args()
@@ -380,6 +382,63 @@ def served_d512_run(gt, flush, rates=(5000.0, 20000.0, 50000.0)):
             "batch_qps": round(B / (statistics.mean(ts) / 1e3), 1), "unit": UNIT,
             "autotune": {k: tune[k] for k in ("cutover", "inflight", "tile_n", "subtract")},
             "serving": served}
+
+
+def large_run(gt, flush, check, max_batch=4096, rho=0.9):
+    """The large form: N = 10M, d = 1000, FP8 rows with per-row scales (FP32
+    masters for the rechecks), 100,000 queries in micro-batches of 4096,
+    heavy-tailed planted duplicates; the margin screen and the oracle's
+    check on a sample of the queries (including the most planted ones)."""
+    import torch
+    import synth
+    free, _ = torch.cuda.mem_get_info()
+    if free < 200e9:
+        return {"skipped": f"needs ~200 GB of free device memory, {free / 1e9:.0f} GB free"}
+    w = synth.WORKLOADS["softmax_n10m_d1000"]
+    rng = np.random.default_rng(5)
+    counts = synth._plant_counts(w, w.n_queries)
+    sample = np.union1d(np.sort(rng.choice(w.n_queries, 12, replace=False)), np.argsort(counts)[-4:])
+    t0 = time.time()
+    ds = synth.generate(w, screen=sample)
+    gen_s = time.time() - t0
+    Fd = torch.from_numpy(ds.F).cuda()
+    t = gt.Tree(Fd, formats=("bf16", "fp8"))
+    del Fd
+    torch.cuda.empty_cache()
+    r = ds.rho_for(rho)
+    Qd, rd = torch.from_numpy(ds.Q).cuda(), torch.from_numpy(r).cuda()
+    stream = torch.cuda.current_stream()
+    B = ds.Q.shape[0]
+    t.query(Qd, rd, dtype="fp8", max_batch=max_batch, results_on_device=True, stream=stream).free()
+    ts = []
+    for _ in range(2):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = t.query(Qd, rd, dtype="fp8", max_batch=max_batch, results_on_device=True,
+                      stream=stream, timing=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+        st = res.stats
+        res.free()
+    out = {"workload": "softmax_n10m_d1000", "N": int(ds.F.shape[0]), "d": int(ds.F.shape[1]),
+           "queries": int(B), "rho": rho, "row_format": "fp8", "micro_batch": max_batch,
+           "value": round(B / (statistics.mean(ts) / 1e3), 1), "unit": UNIT,
+           "ms_per_batch": round(statistics.mean(ts), 2), "micro_batches": st["micro_batches"],
+           "cutover": st["cutover"], "kernel_ms": st["kernel_ms"],
+           "gathered_tests_per_query": st["gathered_tests"] / B, "generate_s": round(gen_s, 1)}
+    if check:
+        import oracle
+        got = t.query(ds.Q[sample], r[sample], dtype="fp8")
+        ref = oracle.brute_force(ds.F, ds.Q[sample], r[sample])
+        out["parity_sample"] = {"queries": int(len(sample)), "oracle": "brute_force (FP64)",
+                                "identical": bool(np.array_equal(got.offsets, ref.offsets)
+                                                  and np.array_equal(got.ids, ref.ids)),
+                                "oracle_ambiguous": int(ref.ambiguous.sum())}
+    t.close()
+    del ds
+    return out
 
 
 def signed_run(gt, flush, check, N=262144, d=256, B=2000, rho=0.8, n_check=64):
@@ -934,6 +993,10 @@ def main():
     if not a.no_serve and not pre and rank == 0 and a.workload == "softmax_n1m_d1000":
         torch.cuda.empty_cache()
         served_d512 = served_d512_run(gt, flush)
+    large = None
+    if not a.no_large and not pre and rank == 0 and a.workload == "softmax_n1m_d1000":
+        torch.cuda.empty_cache()
+        large = large_run(gt, flush, not a.no_cpu)
     streaming = None
     if not a.no_stream and rank == 0:
         streaming = streaming_run(gt, ds, a.dtype, 0.9 if 0.9 in (ds.workload.rhos or ()) else a.rho)
@@ -977,6 +1040,7 @@ def main():
             "comparators": comparators,
             "serving": serving,
             "served_n1m_d512": served_d512,
+            "large_n10m_fp8": large,
             "streaming": streaming,
             "parity_sample": parity,
             "build_s": round(build_s, 3), "generate_s": round(t_gen, 1),
