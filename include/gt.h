@@ -84,7 +84,7 @@ typedef struct gt_tree gt_tree; /* opaque, library-owned device state */
  *                signed q and f (no item is accepted on a bound).  Entries
  *                may be negative (non-finite ones are still GT_EDOMAIN);
  *                d <= 1024; the dense cutover level must be >= 1 and
- *                gt_exhaustive_tree and the server are not available. */
+ *                gt_exhaustive_tree is not available. */
 typedef enum gt_pooling { GT_POOL_SUM = 0, GT_POOL_MAX = 1, GT_POOL_MAXMIN = 2 } gt_pooling;
 
 /* How the pools are stored.
@@ -451,9 +451,10 @@ typedef struct gt_server_stats {
 } gt_server_stats;
 
 /* Create a server over tree t (which must keep BF16 rows; a GT_LAYOUT_PREFIX
- * tree is served at its prefix_level, a GT_POOL_MAXMIN tree is refused).  The
- * server owns its device buffers; the tree must outlive it and is updated in
- * place by queued inserts. */
+ * tree is served at its prefix_level; a GT_POOL_MAXMIN tree takes queries and
+ * inserts of d entries, like gt_query, and is served one level per step).
+ * The server owns its device buffers; the tree must outlive it and is
+ * updated in place by queued inserts. */
 gt_status gt_server_create(gt_tree *t, const gt_server_opts *opts, gt_server **out);
 /* Queue n queries (host Q n x d, rho n, caller tags n); copied on return. */
 gt_status gt_server_submit(gt_server *s, const float *Q, const float *rho, const int64_t *tags,

@@ -167,14 +167,16 @@ gt_status server_alloc(gt_server *S) {
   GT_CUDA(cudaMalloc(&S->rho, (size_t)S->slots * sizeof(float)));
   GT_CUDA(cudaMalloc(&S->thr_keep, (size_t)S->slots * sizeof(float)));
   GT_CUDA(cudaMalloc(&S->thr_acc, (size_t)S->slots * sizeof(float)));
-  GT_CUDA(cudaMalloc(&S->stage, (size_t)S->max_group * (S->t->d + 1) * sizeof(float)));
+  // staging and queues hold the caller's rows (d_in entries: a GT_POOL_MAXMIN
+  // tree stores them split, 2 d_in wide)
+  GT_CUDA(cudaMalloc(&S->stage, (size_t)S->max_group * (S->t->d_in + 1) * sizeof(float)));
   S->ring_cap = S->queue_cap > 0 ? S->queue_cap : std::max<int64_t>(4 * S->max_group, 16384);
-  GT_CUDA(cudaMallocHost(&S->ring_q, (size_t)S->ring_cap * S->t->d * sizeof(float)));
+  GT_CUDA(cudaMallocHost(&S->ring_q, (size_t)S->ring_cap * S->t->d_in * sizeof(float)));
   GT_CUDA(cudaMallocHost(&S->ring_rho, (size_t)S->ring_cap * sizeof(float)));
   S->ring_tag.resize((size_t)S->ring_cap);
   S->ins_cap = 4096;
-  GT_CUDA(cudaMallocHost(&S->ins_h, (size_t)S->ins_cap * S->t->d * sizeof(float)));
-  GT_CUDA(cudaMalloc(&S->ins_d, (size_t)S->ins_cap * S->t->d * sizeof(float)));
+  GT_CUDA(cudaMallocHost(&S->ins_h, (size_t)S->ins_cap * S->t->d_in * sizeof(float)));
+  GT_CUDA(cudaMalloc(&S->ins_d, (size_t)S->ins_cap * S->t->d_in * sizeof(float)));
   for (int h = 0; h < S->cut; ++h)
     for (int p = 0; p < 2; ++p) GT_CUDA(cudaMalloc(&S->lists[h][p], (size_t)S->list_cap * sizeof(Pair)));
   GT_CUDA(cudaMalloc(&S->gemm_out, (size_t)S->list_cap * sizeof(Pair)));
@@ -243,7 +245,6 @@ extern "C" {
 gt_status gt_server_create(gt_tree *t, const gt_server_opts *opts, gt_server **out) {
   if (!t || !out) return set_error(GT_EINVAL, "null argument");
   *out = nullptr;
-  if (t->split_sign) return set_error(GT_EINVAL, "not available for a GT_POOL_MAXMIN tree");
   const bool pre = t->layout == GT_LAYOUT_PREFIX;
   gt_server_opts o;
   std::memset(&o, 0, sizeof(o));
@@ -309,7 +310,7 @@ gt_status gt_server_create(gt_tree *t, const gt_server_opts *opts, gt_server **o
 gt_status gt_server_submit(gt_server *S, const float *Q, const float *rho, const int64_t *tags,
                            int64_t n) {
   if (!S || (n > 0 && (!Q || !rho || !tags))) return set_error(GT_EINVAL, "null argument");
-  const int d = S->t->d;
+  const int d = S->t->d_in;
   for (int64_t i = 0; i < n; ++i) {
     if (!(rho[i] > 0.f) || !(rho[i] <= 1.f)) return set_error(GT_EINVAL, "rho must satisfy 0 < rho <= 1");
   }
@@ -351,7 +352,7 @@ gt_status gt_server_submit(gt_server *S, const float *Q, const float *rho, const
 
 gt_status gt_server_insert(gt_server *S, const float *f, int64_t n) {
   if (!S || (n > 0 && !f)) return set_error(GT_EINVAL, "null argument");
-  const int d = S->t->d;
+  const int d = S->t->d_in;
   if (S->ins_n + n > S->ins_cap) {
     int64_t cap = S->ins_cap;
     while (cap < S->ins_n + n) cap *= 2;
@@ -380,7 +381,7 @@ gt_status gt_server_step(gt_server *S, int64_t *in_flight) {
   const double t0 = now_s();
   // 1. queued inserts, in one batch, before any kernel of this step
   if (S->ins_n > 0) {
-    GT_CUDA(cudaMemcpyAsync(S->ins_d, S->ins_h, (size_t)S->ins_n * t->d * sizeof(float),
+    GT_CUDA(cudaMemcpyAsync(S->ins_d, S->ins_h, (size_t)S->ins_n * t->d_in * sizeof(float),
                             cudaMemcpyHostToDevice, s));
     gt_status st = gt_insert(t, S->ins_d, S->ins_n, s);
     if (st != GT_OK) return st;
@@ -478,7 +479,7 @@ gt_status gt_server_step(gt_server *S, int64_t *in_flight) {
   if (b > 0) {
     const int ring = (int)(fresh - S->groups.data());
     fresh_s0 = (int64_t)ring * S->group_stride;
-    const int d = t->d;
+    const int d = t->d_in;
     // the oldest b queued queries: one or two contiguous pieces of the ring
     const int64_t k0 = S->ring_head, n1 = std::min(b, S->ring_cap - k0), n2 = b - n1;
     GT_CUDA(cudaMemcpyAsync(S->stage, S->ring_q + k0 * d, (size_t)n1 * d * sizeof(float),
@@ -509,7 +510,9 @@ gt_status gt_server_step(gt_server *S, int64_t *in_flight) {
   GT_CUDA(cudaStreamSynchronize(s));
   const uint32_t *hc = S->hcounters;
   if (hc[64 + kFlagTimeout]) return set_error(GT_ETIMEOUT, "a bounded device wait expired");
-  if (hc[64 + kFlagDomain]) return set_error(GT_EDOMAIN, "a query has a negative or non-finite entry");
+  if (hc[64 + kFlagDomain])
+    return set_error(GT_EDOMAIN, t->split_sign ? "a query has a non-finite entry"
+                                               : "a query has a negative or non-finite entry");
   if (hc[64 + kFlagStray]) {
     std::string lv;
     for (auto &g : S->groups)

@@ -46,7 +46,8 @@ def _check_members(res, ds, rho, rng, n=20000):
 def test_paper_scale_1m(gt):
     ds = synth.generate("softmax_n1m_d1000")
     N, B = ds.F.shape[0], ds.Q.shape[0]
-    t = gt.Tree(torch.from_numpy(ds.F).cuda())
+    Fd = torch.from_numpy(ds.F).cuda()
+    t = gt.Tree(Fd)
     rng = np.random.default_rng(11)
     sample = np.sort(rng.choice(B, 48, replace=False))
     Qd = torch.from_numpy(ds.Q).cuda()
@@ -67,6 +68,9 @@ def test_paper_scale_1m(gt):
         ex = t.exhaustive(Qd[sample], rd[sample])
         ref = oracle.brute_force(ds.F, ds.Q[sample], rho[sample])
         assert np.array_equal(ex.offsets, ref.offsets) and np.array_equal(ex.ids, ref.ids)
+        # the Exh comparator over the raw rows (no tree), in the bench's form
+        raw = gt.exhaustive(Fd, Qd[sample], rd[sample])
+        assert np.array_equal(raw.offsets, ref.offsets) and np.array_equal(raw.ids, ref.ids)
     t.close()
 
 

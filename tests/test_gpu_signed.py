@@ -139,8 +139,8 @@ def test_signed_domain_and_refusals(gt):
     with pytest.raises(gt.GTError) as e:                 # so is a cutover at the items
         t.query(Q, 0.8, cutover=0)
     assert e.value.status == 1
-    with pytest.raises(gt.GTError) as e:
-        gt.Server(t)
+    with pytest.raises(gt.GTError) as e:                 # no drain schedule (max pools)
+        gt.Server(t, schedule="drain")
     assert e.value.status == 1
     bad = Q.copy()
     bad[2, 5] = np.nan
@@ -158,4 +158,41 @@ def test_signed_domain_and_refusals(gt):
     with pytest.raises(gt.GTError) as e:                 # sum pools still refuse negatives
         gt.Tree(F)
     assert e.value.status == 2
+    t.close()
+
+
+def test_signed_served_exact_with_inserts(gt):
+    # the continuous-batching server over split rows: queries and inserts of
+    # d entries, one level per step, every answer the exact set over the
+    # items present when its group was admitted
+    F, Q = workload(6000, 48, 120, seed=31)
+    rho = np.full(Q.shape[0], 0.8, dtype=np.float32)
+    rho[::4] = np.float32(0.75)
+    t = gt.Tree(F[:5000], capacity=5500, pooling="maxmin")
+    srv = gt.Server(t, dtype="bf16", max_group=16)
+    assert srv.stats()["schedule"] == 1
+    done, nxt, ins, step = {}, 0, 5000, 0
+    while len(done) < Q.shape[0]:
+        if nxt < Q.shape[0]:
+            srv.submit(Q[nxt:nxt + 10], rho[nxt:nxt + 10], np.arange(nxt, min(nxt + 10, Q.shape[0])))
+            nxt += 10
+        if step % 3 == 0 and ins < F.shape[0]:
+            srv.insert(F[ins:ins + 100])                 # grows the storage past 5500
+            ins += 100
+        srv.step()
+        for tag, ids, snap in srv.poll():
+            done[tag] = (ids, snap)
+        step += 1
+        assert step < 2000
+    srv.close()
+    snaps = {}
+    for tag, (ids, snap) in done.items():
+        snaps.setdefault(snap, []).append(tag)
+    assert len(snaps) >= 3
+    for snap, tags in snaps.items():
+        tags = np.array(sorted(tags))
+        ref = oracle.brute_force(F[:snap], Q[tags], rho[tags])
+        assert ref.ambiguous.sum() == 0
+        for i, tag in enumerate(tags):
+            assert np.array_equal(done[tag][0], ref.neighbours(i)), f"query {tag} (N={snap})"
     t.close()
