@@ -489,6 +489,34 @@ gt_status gt_set_sm_limit(gt_tree *t, int32_t n);
  * (its implementation runs on a CPU). */
 gt_status gt_set_wait_expiry(gt_tree *t, int32_t on);
 
+/* What a tree is: its sizes, row formats and how its pools are formed. */
+typedef struct gt_tree_info {
+  int64_t n_items;       /* N */
+  int64_t capacity;      /* items held before an insert must grow the storage */
+  int32_t d;             /* entries per input row */
+  int32_t row_width;     /* entries per stored row (2d for GT_POOL_MAXMIN) */
+  int32_t levels;        /* L + 1 */
+  int32_t pooling;       /* gt_pooling */
+  int32_t layout;        /* gt_layout */
+  int32_t prefix_level;  /* GT_LAYOUT_PREFIX: c (else 0) */
+  uint32_t formats;      /* bitmask of (1 << gt_dtype) row formats kept */
+  int32_t device;        /* CUDA device of the tree's memory */
+} gt_tree_info;
+gt_status gt_info(const gt_tree *t, gt_tree_info *out);
+
+/* Checkpoint (the paper builds its index offline, Sec. 2; a built or grown
+ * tree can be kept and reopened): gt_save writes to the file at `path` what
+ * gt_load needs to rebuild the same tree - the stored item rows (FP32, in
+ * tree order), the tree permutation, the build options (pooling, layout,
+ * prefix level, formats, capacity) and the tuning choices.  gt_load rebuilds
+ * it on the current device: rows, pools of every level and the ids returned
+ * are bit for bit those of the saved tree (the build is deterministic).
+ * Errors: GT_EINVAL for a bad argument, a file that cannot be opened, read or
+ * written (gt_last_error gives the reason) or that is not a tree checkpoint;
+ * GT_ENOMEM / GT_ECUDA as for gt_build.  stream: cudaStream_t or NULL. */
+gt_status gt_save(const gt_tree *t, const char *path);
+gt_status gt_load(const char *path, void *stream, gt_tree **out);
+
 int64_t gt_size(const gt_tree *t);        /* current N */
 int32_t gt_dim(const gt_tree *t);         /* d */
 int32_t gt_levels(const gt_tree *t);      /* L + 1 = ceil(log2 N) + 1 */

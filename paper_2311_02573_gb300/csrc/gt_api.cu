@@ -1,6 +1,7 @@
 // The C ABI of include/gt.h: argument checks, staging of host inputs,
 // micro-batching of the query traversal, and error reporting.
 #include <algorithm>
+#include <cerrno>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -285,6 +286,7 @@ extern "C" {
 const char *gt_last_error(void) { return g_err.c_str(); }
 
 gt_status gt_build(const float *F, int64_t N, int32_t d, const gt_build_opts *opts, gt_tree **out) {
+  TraceRange trace("gt_build");
   if (!out) return set_error(GT_EINVAL, "null output handle");
   *out = nullptr;
   if (!F) return set_error(GT_EINVAL, "null F");
@@ -386,6 +388,7 @@ gt_status gt_build(const float *F, int64_t N, int32_t d, const gt_build_opts *op
 }
 
 gt_status gt_insert(gt_tree *t, const float *f, int64_t n_new, void *stream) {
+  TraceRange trace("gt_insert");
   if (!t) return set_error(GT_EINVAL, "null tree");
   if (n_new == 0) return GT_OK;
   if (!f || n_new < 0) return set_error(GT_EINVAL, "bad insert arguments");
@@ -471,6 +474,7 @@ static gt_status run_search(gt_tree *t, const float *Q, int64_t B, const float *
 static gt_status run_search_on(gt_tree *t, const float *Q, int64_t B, const float *rho,
                                const gt_query_opts *opts, gt_csr *out, bool exhaustive,
                                cudaStream_t s) {
+  TraceRange trace("gt_query");
   if (!t || !out) return set_error(GT_EINVAL, "null tree or output");
   std::memset(out, 0, sizeof(*out));
   if (B < 0) return set_error(GT_EINVAL, "negative query count");
@@ -650,6 +654,7 @@ static gt_status run_search_on(gt_tree *t, const float *Q, int64_t B, const floa
   int64_t q0 = 0;
   while (q0 < B) {
     const int64_t b = std::min(bm, B - q0);
+    TraceRange trace_mb("micro-batch");
     // everything one micro-batch does on the device, in stream order
     int64_t n_launch = 0, n_level = 0;
     auto enqueue = [&](KernelTimer &tmr) -> gt_status {
@@ -969,6 +974,7 @@ gt_status gt_exhaustive_tree(gt_tree *t, const float *Q, int64_t B, const float 
 
 gt_status gt_exhaustive(const float *F, int64_t N, int32_t d, const float *Q, int64_t B,
                         const float *rho, const gt_query_opts *opts, gt_csr *out) {
+  TraceRange trace("gt_exhaustive");
   if (!out) return set_error(GT_EINVAL, "null output");
   std::memset(out, 0, sizeof(*out));
   if (!F) return set_error(GT_EINVAL, "null F");
@@ -1106,6 +1112,7 @@ gt_status gt_pair_bounds(gt_tree *t, int32_t level, int32_t dtype, const float *
 
 gt_status gt_autotune(gt_tree *t, const float *Q, int64_t B, const float *rho, int32_t dtype,
                       void *stream, gt_autotune_result *out) {
+  TraceRange trace("gt_autotune");
   if (!t || !Q || !rho || B < 1) return set_error(GT_EINVAL, "bad autotune arguments");
   const bool pre = t->layout == GT_LAYOUT_PREFIX;
   if (dtype < GT_F32 || dtype > GT_FP8 || !(t->formats & (1u << dtype)))
@@ -1317,6 +1324,180 @@ gt_status gt_set_sm_limit(gt_tree *t, int32_t n) {
 gt_status gt_set_wait_expiry(gt_tree *t, int32_t on) {
   if (!t) return set_error(GT_EINVAL, "null tree");
   t->expire_waits = on ? 1 : 0;
+  return GT_OK;
+}
+
+gt_status gt_info(const gt_tree *t, gt_tree_info *out) {
+  if (!t || !out) return set_error(GT_EINVAL, "null argument");
+  std::memset(out, 0, sizeof(*out));
+  out->n_items = t->N;
+  out->capacity = t->cap;
+  out->d = t->d_in;
+  out->row_width = t->d;
+  out->levels = t->L + 1;
+  out->pooling = t->split_sign ? GT_POOL_MAXMIN : t->pooling;
+  out->layout = t->layout;
+  out->prefix_level = t->layout == GT_LAYOUT_PREFIX ? t->pc : 0;
+  out->formats = t->formats;
+  out->device = t->device;
+  return GT_OK;
+}
+
+// Checkpoint file: this header, the tree permutation (N int32), then the
+// stored item rows (N x row width FP32, tree order), all little-endian.
+namespace {
+struct CkptHeader {
+  char magic[8];
+  int64_t n, cap;
+  int32_t d, d_in, pooling, layout, pc, split_sign;
+  uint32_t formats;
+  int32_t tuned_cut[3], tuned_g[3], tuned_bn, tuned_sub[3];
+  int32_t reserved[5];
+};
+constexpr char kCkptMagic[8] = {'G', 'T', 'T', 'R', 'E', 'E', '1', 0};
+constexpr int64_t kCkptChunkRows = 16384;
+
+struct File {
+  FILE *f = nullptr;
+  ~File() {
+    if (f) std::fclose(f);
+  }
+};
+}  // namespace
+
+gt_status gt_save(const gt_tree *t, const char *path) {
+  if (!t || !path) return set_error(GT_EINVAL, "null argument");
+  CkptHeader h;
+  std::memset(&h, 0, sizeof(h));
+  std::memcpy(h.magic, kCkptMagic, sizeof(h.magic));
+  h.n = t->N;
+  h.cap = t->cap;
+  h.d = t->d;
+  h.d_in = t->d_in;
+  h.pooling = t->pooling;
+  h.layout = t->layout;
+  h.pc = t->pc;
+  h.split_sign = t->split_sign ? 1 : 0;
+  h.formats = t->formats;
+  for (int i = 0; i < 3; ++i) {
+    h.tuned_cut[i] = t->tuned_cut[i];
+    h.tuned_g[i] = t->tuned_g[i];
+    h.tuned_sub[i] = t->tuned_sub[i];
+  }
+  h.tuned_bn = t->tuned_bn;
+  std::vector<int32_t> perm((size_t)t->N);
+  GT_CUDA(cudaMemcpy(perm.data(), t->perm, (size_t)t->N * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  File f;
+  f.f = std::fopen(path, "wb");
+  if (!f.f) return set_error(GT_EINVAL, std::string("cannot open ") + path + ": " + std::strerror(errno));
+  bool ok = std::fwrite(&h, sizeof(h), 1, f.f) == 1 &&
+            std::fwrite(perm.data(), sizeof(int32_t), perm.size(), f.f) == perm.size();
+  std::vector<float> rows;
+  for (int64_t r0 = 0; ok && r0 < t->N; r0 += kCkptChunkRows) {
+    const int64_t n = std::min<int64_t>(kCkptChunkRows, t->N - r0);
+    rows.resize((size_t)n * t->d);
+    GT_CUDA(cudaMemcpy2D(rows.data(), (size_t)t->d * sizeof(float), t->rows32 + (size_t)r0 * t->stride,
+                         (size_t)t->stride * sizeof(float), (size_t)t->d * sizeof(float), (size_t)n,
+                         cudaMemcpyDeviceToHost));
+    ok = std::fwrite(rows.data(), sizeof(float), rows.size(), f.f) == rows.size();
+  }
+  if (!ok || std::fflush(f.f) != 0)
+    return set_error(GT_EINVAL, std::string("cannot write ") + path + ": " + std::strerror(errno));
+  return GT_OK;
+}
+
+gt_status gt_load(const char *path, void *stream, gt_tree **out) {
+  if (!path || !out) return set_error(GT_EINVAL, "null argument");
+  *out = nullptr;
+  TraceRange trace("gt_load");
+  File f;
+  f.f = std::fopen(path, "rb");
+  if (!f.f) return set_error(GT_EINVAL, std::string("cannot open ") + path + ": " + std::strerror(errno));
+  CkptHeader h;
+  if (std::fread(&h, sizeof(h), 1, f.f) != 1 || std::memcmp(h.magic, kCkptMagic, sizeof(h.magic)) != 0)
+    return set_error(GT_EINVAL, std::string(path) + " is not a tree checkpoint");
+  const bool pre = h.layout == GT_LAYOUT_PREFIX;
+  if (h.n < 1 || h.cap < h.n || h.cap >= ((int64_t)1 << 31) || h.d < 1 || h.d > 2048 ||
+      h.d_in < 1 || h.d != (h.split_sign ? 2 * h.d_in : h.d_in) ||
+      (h.layout != GT_LAYOUT_TREE && !pre) || (h.pooling != GT_POOL_SUM && h.pooling != GT_POOL_MAX) ||
+      (pre && (h.pc < 1 || h.pc > 12)))
+    return set_error(GT_EINVAL, std::string(path) + ": inconsistent checkpoint header");
+  std::vector<int32_t> perm((size_t)h.n);
+  if (std::fread(perm.data(), sizeof(int32_t), perm.size(), f.f) != perm.size())
+    return set_error(GT_EINVAL, std::string(path) + ": truncated checkpoint");
+  prepare_level_kernels();
+  gt_tree *t = new gt_tree();
+  t->N = h.n;
+  t->d = h.d;
+  t->d_in = h.d_in;
+  t->split_sign = h.split_sign != 0;
+  t->L = top_level(h.n);
+  t->stride = ((int64_t)t->d + 63) / 64 * 64;
+  t->formats = h.formats;
+  t->pooling = h.pooling;
+  t->layout = h.layout;
+  t->pc = pre ? h.pc : 0;
+  for (int i = 0; i < 3; ++i) {
+    t->tuned_cut[i] = h.tuned_cut[i];
+    t->tuned_g[i] = h.tuned_g[i];
+    t->tuned_sub[i] = h.tuned_sub[i];
+  }
+  t->tuned_bn = h.tuned_bn;
+  t->stream = (cudaStream_t)stream;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  t->device = dev;
+  cudaDeviceGetAttribute(&t->sm_count, cudaDevAttrMultiProcessorCount, dev);
+  t->sm_total = t->sm_count;
+  cudaStream_t s = t->stream;
+  gt_status st = pre ? prefix_alloc(t, h.cap) : tree_alloc(t, h.cap);
+  float *stage = nullptr;
+  if (st == GT_OK) {
+    cudaError_t e = cudaMalloc(&stage, (size_t)kCkptChunkRows * t->d * sizeof(float));
+    if (e != cudaSuccess) st = cuda_error(e, "checkpoint staging");
+  }
+  std::vector<float> rows;
+  for (int64_t r0 = 0; st == GT_OK && r0 < t->N; r0 += kCkptChunkRows) {
+    const int64_t n = std::min<int64_t>(kCkptChunkRows, t->N - r0);
+    rows.resize((size_t)n * t->d);
+    if (std::fread(rows.data(), sizeof(float), rows.size(), f.f) != rows.size()) {
+      st = set_error(GT_EINVAL, std::string(path) + ": truncated checkpoint");
+      break;
+    }
+    cudaError_t e = cudaMemcpyAsync(stage, rows.data(), rows.size() * sizeof(float),
+                                    cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) {
+      st = cuda_error(e, "checkpoint rows");
+      break;
+    }
+    st = tree_build_level0(t, stage, r0, n, nullptr, s, true);
+    if (st == GT_OK) {
+      e = cudaStreamSynchronize(s);  // the host buffer is refilled next
+      if (e != cudaSuccess) st = cuda_error(e, "checkpoint rows");
+    }
+  }
+  int hflags[kFlagCount] = {0};
+  if (st == GT_OK) st = read_flags(t, s, hflags);
+  if (st == GT_OK && hflags[kFlagDomain])
+    st = set_error(GT_EINVAL, std::string(path) + ": a stored row has a negative or non-finite entry");
+  // the ids: the saved tree permutation (the level-0 pass wrote positions)
+  if (st == GT_OK) {
+    cudaError_t e = cudaMemcpyAsync(t->perm, perm.data(), perm.size() * sizeof(int32_t),
+                                    cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) st = cuda_error(e, "checkpoint permutation");
+  }
+  if (st == GT_OK) st = pre ? prefix_build(t, 0, t->N, s) : tree_build_levels(t, 0, t->N, s);
+  if (st == GT_OK) {
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_error(e, "checkpoint build");
+  }
+  cudaFree(stage);
+  if (st != GT_OK) {
+    gt_free(t);
+    return st;
+  }
+  t->max_norm_dev = tree_norm_dev(t);
+  *out = t;
   return GT_OK;
 }
 

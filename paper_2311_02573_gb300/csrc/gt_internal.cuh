@@ -5,6 +5,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <string>
@@ -14,6 +15,15 @@
 #include "../../include/gt.h"
 
 namespace gt {
+
+// A named NVTX range for the lifetime of the object (host-side tracing of the
+// entry points and of each micro-batch; free when no tool is attached).
+struct TraceRange {
+  explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange &) = delete;
+  TraceRange &operator=(const TraceRange &) = delete;
+};
 
 constexpr int kMaxLevels = 40;
 // counter slots after the levels: [40] results, [41] rechecks, [42] refines,
@@ -206,7 +216,8 @@ bool is_device_ptr(const void *p);
 // tree kernels (gt_tree.cu)
 gt_status tree_alloc(gt_tree *t, int64_t cap);
 gt_status tree_build_level0(gt_tree *t, const float *F_dev, int64_t first, int64_t n,
-                            const int32_t *perm_dev_or_null, cudaStream_t s);
+                            const int32_t *perm_dev_or_null, cudaStream_t s,
+                            bool stored_rows = false);
 gt_status tree_build_levels(gt_tree *t, int64_t first_item, int64_t n_items, cudaStream_t s);
 float tree_norm_dev(gt_tree *t);
 // prefix layout (gt_tree.cu): storage for `cap` items, and the prefix rows and

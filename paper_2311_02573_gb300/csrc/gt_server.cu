@@ -376,6 +376,7 @@ gt_status gt_server_insert(gt_server *S, const float *f, int64_t n) {
 
 gt_status gt_server_step(gt_server *S, int64_t *in_flight) {
   if (!S) return set_error(GT_EINVAL, "null server");
+  TraceRange trace("gt_server_step");
   gt_tree *t = S->t;
   cudaStream_t s = S->s;
   const double t0 = now_s();

@@ -337,15 +337,17 @@ gt_status tree_alloc(gt_tree *t, int64_t cap) {
 }
 
 gt_status tree_build_level0(gt_tree *t, const float *F_dev, int64_t first, int64_t n,
-                            const int32_t *perm_dev, cudaStream_t s) {
+                            const int32_t *perm_dev, cudaStream_t s, bool stored_rows) {
   if (n <= 0) return GT_OK;
   RowsOut o = rows_out(t);
-  // level-0 rows start at row 0
+  // level-0 rows start at row 0; rows already in the stored form (a
+  // checkpoint's) are t->d wide and are not split again
   const int kv = kv4_for(t->stride);
   unsigned *nb = reinterpret_cast<unsigned *>(t->flags + 32);
   int blocks = (int)std::min<int64_t>((n + 7) / 8, (int64_t)t->sm_count * 8);
-  GT_DISPATCH_KV4(kv, k_level0<KV><<<blocks, 256, 0, s>>>(F_dev, first, n, t->d_in,
-                                                          t->split_sign ? 1 : 0, perm_dev,
+  const int d_in = stored_rows ? t->d : t->d_in;
+  const int split = (t->split_sign && !stored_rows) ? 1 : 0;
+  GT_DISPATCH_KV4(kv, k_level0<KV><<<blocks, 256, 0, s>>>(F_dev, first, n, d_in, split, perm_dev,
                                                           t->perm, o, t->flags, nb));
   GT_CUDA(cudaGetLastError());
   return GT_OK;

@@ -87,6 +87,15 @@ class ServerStats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class TreeInfo(ctypes.Structure):
+    _fields_ = [("n_items", _c_i64), ("capacity", _c_i64), ("d", _c_i32), ("row_width", _c_i32),
+                ("levels", _c_i32), ("pooling", _c_i32), ("layout", _c_i32),
+                ("prefix_level", _c_i32), ("formats", _c_u32), ("device", _c_i32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class GTError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -99,7 +108,7 @@ ENTRY_POINTS = ("gt_build", "gt_insert", "gt_query", "gt_query_into", "gt_exhaus
                 "gt_dense_scores", "gt_pair_bounds", "gt_query_static", "gt_server_create", "gt_server_submit",
                 "gt_server_insert", "gt_server_step", "gt_server_poll", "gt_server_get_stats",
                 "gt_server_free", "gt_autotune", "gt_set_tuning", "gt_set_wait_expiry",
-                "gt_set_sm_limit",
+                "gt_set_sm_limit", "gt_info", "gt_save", "gt_load",
                 "gt_size", "gt_dim", "gt_levels", "gt_free", "gt_csr_free", "gt_last_error")
 
 
@@ -150,6 +159,12 @@ def load(build_if_missing: bool = True):
     lib.gt_set_wait_expiry.restype = _c_i32
     lib.gt_set_sm_limit.argtypes = [P, _c_i32]
     lib.gt_set_sm_limit.restype = _c_i32
+    lib.gt_info.argtypes = [P, ctypes.POINTER(TreeInfo)]
+    lib.gt_info.restype = _c_i32
+    lib.gt_save.argtypes = [P, ctypes.c_char_p]
+    lib.gt_save.restype = _c_i32
+    lib.gt_load.argtypes = [ctypes.c_char_p, P, ctypes.POINTER(P)]
+    lib.gt_load.restype = _c_i32
     lib.gt_server_free.argtypes = [P]
     lib.gt_server_free.restype = None
     for f in ("gt_build", "gt_insert", "gt_query", "gt_exhaustive", "gt_exhaustive_tree",
@@ -451,6 +466,29 @@ class Tree:
         """gt_set_tuning: pin the cutover level, tests in flight, GEMM tile."""
         _check(load().gt_set_tuning(self._h, DTYPES[dtype] if isinstance(dtype, str) else dtype,
                                     cutover, inflight, tile))
+
+    def info(self) -> dict:
+        """gt_info: sizes, row formats, pooling and layout of the tree."""
+        r = TreeInfo()
+        _check(load().gt_info(self._h, ctypes.byref(r)))
+        return r.as_dict()
+
+    def save(self, path: str):
+        """gt_save: write a checkpoint gt_load rebuilds the same tree from."""
+        _check(load().gt_save(self._h, os.fsencode(path)))
+
+    @classmethod
+    def load(cls, path: str, stream=None) -> "Tree":
+        """gt_load: rebuild a tree from a checkpoint written by save()."""
+        h = _c_p()
+        _check(load().gt_load(os.fsencode(path), _stream_ptr(stream), ctypes.byref(h)))
+        t = object.__new__(cls)
+        t._h = h
+        info = t.info()
+        t.layout = info["layout"]
+        t.prefix_level = info["prefix_level"]
+        t.row_width = info["row_width"]
+        return t
 
     def set_sm_limit(self, n: int):
         """gt_set_sm_limit: size later calls' grids for at most n SMs (0: all),

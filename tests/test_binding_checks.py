@@ -60,3 +60,15 @@ def test_query_static_refuses_bad_arguments(fake_tree, case, exc):
     # "host": every argument is well formed but lives in host memory
     with pytest.raises(exc):
         fake_tree.query_static(Q, rho, off, ids)
+
+
+def test_load_refuses_files_that_are_not_checkpoints(tmp_path):
+    # checked before any device work: runs without a GPU
+    from paper_2311_02573_gb300 import build, gt
+    build.build()
+    bad = tmp_path / "not_a_tree.gt"
+    bad.write_bytes(b"this is not a tree checkpoint" * 8)
+    for path in (str(bad), str(tmp_path / "missing.gt")):
+        with pytest.raises(gt.GTError) as e:
+            gt.Tree.load(path)
+        assert e.value.status == 1

@@ -46,3 +46,4 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(gt.ServerOpts) == 8 + 4 + 4 + 8 + 8 + 8 + 4 + 4
     assert gt.ServerOpts.schedule.offset == 40
     assert ctypes.sizeof(gt.ServerStats) == 16 * 8
+    assert ctypes.sizeof(gt.TreeInfo) == 8 + 8 + 4 * 8
