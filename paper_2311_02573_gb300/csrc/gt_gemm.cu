@@ -79,6 +79,9 @@ struct DenseArgs {
   int64_t ld;
   int *flags;
   float cu_up;         // mode 3: upper bound on a pool's exact score = acc * cu_up
+  float cl_dn;         // mode 3: lower bound on a pool's exact score = acc * cl_dn
+  int pad_lower;       // mode 3: the entry's fourth word holds that lower bound (tree
+                       // layout) rather than the raw score (prefix layout)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -308,8 +311,14 @@ __device__ __forceinline__ void epilogue_tile(const DenseArgs &a, uint32_t tcol,
             SibPair e;
             e.q = q;
             e.p = m0 + i;
-            e.U = __fmul_ru(__uint_as_float(pick32(r, hh, i)), a.cu_up);
-            e.pad = pick32(r, hh, i);  // the raw score (the prefix layout's block total)
+            const float raw = __uint_as_float(pick32(r, hh, i));
+            e.U = __fmul_ru(raw, a.cu_up);
+            // tree layout: the pool's lower bound (none for the level's last
+            // pool, the one pool an insert can extend while a served group
+            // still holds this entry); prefix layout: the raw score, the
+            // block total the splits below difference against
+            e.pad = !a.pad_lower ? pick32(r, hh, i)
+                                 : __float_as_uint(m0 + i + 1u < a.n_pools ? __fmul_rd(raw, a.cl_dn) : 0.f);
             if (pos < a.out_cap) o[pos] = e;
           }
         }
@@ -992,7 +1001,13 @@ gt_status launch_dense_impl(gt_tree *t, int h, int mode, int64_t q0, int64_t b, 
     float c = (float)cu;
     if ((double)c < cu) c = std::nextafter(c, INFINITY);
     a.cu_up = c;
+    float l = (float)cl;
+    if ((double)l > cl) l = std::nextafter(l, 0.0f);
+    a.cl_dn = l;
   }
+  // the lower bounds feed the accept test of left items reached by
+  // subtraction (sum pools only; a signed tree accepts nothing from bounds)
+  a.pad_lower = t->layout != GT_LAYOUT_PREFIX && t->pooling == GT_POOL_SUM && !t->split_sign;
   const int bmc = (shape == 2 || shape == 3) ? 256 : 128, bn = shape == 1 ? 128 : 256;
   const int64_t tiles = ((b + bmc - 1) / bmc) * ((rows + bn - 1) / bn);
   const int grid = shape == 3 ? 2 * (int)std::max<int64_t>(

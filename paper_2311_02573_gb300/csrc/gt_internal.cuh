@@ -47,9 +47,12 @@ struct __align__(8) Pair {
   uint32_t q, j;
 };
 
-// (query, parent pool, upper bound on the parent's exact score): the
-// subtraction path tests one child of the parent and bounds the other as
+// (query, parent pool, upper and lower bounds on the parent's exact score):
+// the subtraction path tests one child of the parent and bounds the other as
 // parent minus the tested child (Sec. 2: the left half's score is sim - rsim).
+// The fourth word holds the lower bound as FP32 bits (0, which accepts
+// nothing, where none is known); the prefix layout's entries hold the prefix
+// score at the pool's end there instead.
 struct __align__(16) SibPair {
   uint32_t q, p;
   float U;

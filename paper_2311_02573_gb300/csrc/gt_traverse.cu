@@ -488,8 +488,7 @@ __global__ void __launch_bounds__(256) k_level(const LevelArgs a) {
 // its upper bound Ur and the left child's bound Ul = Up - L_right (rounded up).
 template <int FMT>
 __device__ __forceinline__ void sub_test(const LevelArgs &a, float acc, uint32_t r, float qn1,
-                                         float Up, float &Ul, float &Ur) {
-  float Lr;
+                                         float Up, float &Ul, float &Ur, float &Lr) {
   test_bounds<FMT>(a, acc, r, qn1, Ur, Lr);
   // The last row of a level is the one pool an insert can extend after its
   // parent's bound was taken (a server group keeps the tree of its admission
@@ -499,14 +498,29 @@ __device__ __forceinline__ void sub_test(const LevelArgs &a, float acc, uint32_t
   Ul = __fsub_ru(Up, fmaxf(Lr, 0.f));
 }
 
+// Subtraction path, the children's lower bounds.  The tested (right) child
+// keeps its own row's lower bound Lr, except when that row is the level's last
+// (the one pool an insert can extend while a served group still holds the
+// entry: the current row may then hold members the entry's pool lacks).  The
+// other child's exact score is the parent's minus the tested child's, so
+// Ll = L_parent - U_right (rounded down) bounds it from below; with no right
+// child the left child is the parent's whole pool.  0 is a valid lower bound
+// of every (non-negative) score and accepts nothing.
+__device__ __forceinline__ void sub_lower(float Lp, bool has_r, bool r_last, float Ur, float Lr_row,
+                                          float &Ll, float &Lr) {
+  Ll = has_r ? fmaxf(__fsub_rd(Lp, Ur), 0.f) : Lp;
+  Lr = (has_r && !r_last) ? fmaxf(Lr_row, 0.f) : 0.f;
+}
+
 // Subtraction path, a warp's output: lane i holds entry e of its batch;
 // bit i of m_left / m_right says whether that entry's children survive, with
-// bounds my_ul / my_ur.  Survivors become entries for the next level, or at
-// the leaves the item pairs of the surviving level-1 pools.
+// bounds my_ul / my_ur (upper) and my_ll / my_lr (lower).  Survivors become
+// entries for the next level, or at the leaves the item pairs of the
+// surviving level-1 pools.
 template <bool TO_LEAF>
 __device__ __forceinline__ void sub_emit(const LevelArgs &a, void *out_v, const SibPair &e,
                                          uint32_t m_left, uint32_t m_right, float my_ul,
-                                         float my_ur) {
+                                         float my_ur, float my_ll, float my_lr) {
   const int lane = threadIdx.x & 31;
   const bool kl = (m_left >> lane) & 1u, kr = (m_right >> lane) & 1u;
   const uint32_t c_l = 2u * e.p, c_r = 2u * e.p + 1u;
@@ -558,9 +572,15 @@ __device__ __forceinline__ void sub_emit(const LevelArgs &a, void *out_v, const 
         if ((uint64_t)pos + tot > a.out_cap) atomicExch(&a.flags[kFlagOverflow], 1);
         SibPair x;
         x.q = e.q;
-        x.pad = 0;
-        if (kl) { x.p = c_l; x.U = my_ul; if (pos < a.out_cap) out[pos] = x; ++pos; }
-        if (kr) { x.p = c_r; x.U = my_ur; if (pos < a.out_cap) out[pos] = x; }
+        if (kl) {
+          x.p = c_l; x.U = my_ul; x.pad = __float_as_uint(my_ll);
+          if (pos < a.out_cap) out[pos] = x;
+          ++pos;
+        }
+        if (kr) {
+          x.p = c_r; x.U = my_ur; x.pad = __float_as_uint(my_lr);
+          if (pos < a.out_cap) out[pos] = x;
+        }
       }
     }
   }
@@ -633,11 +653,13 @@ __global__ void __launch_bounds__(256) k_level_sub(const LevelArgs a, const SibP
     }
     const int cnt = (int)min(32u, n - base);
     float my_ul = 0.f, my_ur = 0.f;   // bounds of this lane's entry's children
+    float my_ll = 0.f, my_lr = 0.f;
     uint32_t m_left = 0, m_right = 0;
     for (int i = 0; i < cnt; ++i) {
       const uint32_t q = __shfl_sync(FULL, e.q, i);
       const uint32_t p = __shfl_sync(FULL, e.p, i);
       const float Up = __shfl_sync(FULL, e.U, i);
+      const float Lp = __uint_as_float(__shfl_sync(FULL, e.pad, i));
       if (q != cur_q) {
         cur_q = q;
         const float4 *qrow = reinterpret_cast<const float4 *>(a.qf32 + (size_t)q * a.qstride);
@@ -657,7 +679,7 @@ __global__ void __launch_bounds__(256) k_level_sub(const LevelArgs a, const SibP
         rho = a.rho[q];
       }
       const uint32_t r = 2u * p + 1u;
-      float Ul = Up, Ur = 0.f;
+      float Ul = Up, Ur = 0.f, Lr = 0.f;
       const bool has_r = r < a.n_rows;
       if (has_r) {
         const uint8_t *row = a.rows + (size_t)r * a.row_bytes;
@@ -669,16 +691,17 @@ __global__ void __launch_bounds__(256) k_level_sub(const LevelArgs a, const SibP
         }
         float acc = row_dot<FMT, KV, false>(w, qreg, nullptr, a.nvec);
         acc = warp_sum(acc);
-        sub_test<FMT>(a, acc, r, qn1, Up, Ul, Ur);
+        sub_test<FMT>(a, acc, r, qn1, Up, Ul, Ur, Lr);
       }
       if (Ul >= rho) m_left |= 1u << i;
       if (has_r && Ur >= rho) m_right |= 1u << i;
       if (lane == i) {
         my_ul = Ul;
         my_ur = Ur;
+        sub_lower(Lp, has_r, r + 1u >= a.n_rows, Ur, Lr, my_ll, my_lr);
       }
     }
-    sub_emit<TO_LEAF>(a, out_v, e, m_left, m_right, my_ul, my_ur);
+    sub_emit<TO_LEAF>(a, out_v, e, m_left, m_right, my_ul, my_ur, my_ll, my_lr);
   }
   raise_stray(a, stray);
 }
@@ -820,6 +843,9 @@ __global__ void __launch_bounds__(32 * kRingWarps, 1)
         stray = true;
         e.q = 0; e.p = 0;
       }
+      // MODE 4 reads the bounds again after the batch (fewer registers held
+      // across the loop)
+      if (MODE == 4) { e.U = 0.f; e.pad = 0; }
       const uint32_t r = 2u * e.p + 1u;
       if (r < a.n_rows) row = r;
     } else {
@@ -907,7 +933,8 @@ __global__ void __launch_bounds__(32 * kRingWarps, 1)
     uint32_t m_a = 0, m_b = 0;   // pass / recheck, or left / right survives
     uint32_t m_c = 0;            // MODE 4: the left item is tested next
     uint32_t m_d = 0;            // FP8 leaves: re-scored by the BF16 pass
-    float my_ul = 0.f, my_ur = 0.f;
+    uint32_t m_e = 0;            // MODE 4: the left item accepted on its lower bound
+    float my_ul = 0.f, my_ur = 0.f, my_ll = 0.f, my_lr = 0.f;
     // At the pool levels (modes 0, 2, 3, 5) the per-pair loop only gathers
     // and scores: wait for the row, dot product, refill the slot, warp sum.
     // The score of pair i is kept by lane i, and after the batch every lane
@@ -973,16 +1000,12 @@ __global__ void __launch_bounds__(32 * kRingWarps, 1)
         decide<FMT, KV, true, false>(a, acc, rowi, qn1, rho, qreg, nullptr, (int)i, m_a, m_b, m_d,
                                      n_refine);
       } else if (MODE == 4) {
-        // the right item decided; the left item's bound is the pool's minus
-        // the right item's lower bound
-        const float Up = __shfl_sync(FULL, e_cur.U, i);
-        float Ul = Up, Ur = 0.f;
-        if (has) {
+        // the right item decided here; its score kept by lane i, which bounds
+        // the left item after the batch
+        if (has)
           decide<FMT, KV, true, false>(a, acc, rowi, qn1, rho, qreg, nullptr, (int)i, m_a, m_b, m_d,
                                        n_refine);
-          sub_test<FMT>(a, acc, rowi, qn1, Up, Ul, Ur);
-        }
-        if (Ul >= rho) m_c |= 1u << i;
+        if ((uint32_t)lane == i) my_acc = acc;
       } else if ((uint32_t)lane == i) {
         my_acc = acc;
       }
@@ -1009,7 +1032,34 @@ __global__ void __launch_bounds__(32 * kRingWarps, 1)
         m_b = __ballot_sync(FULL, has && U >= rho_l);
         my_ul = Ul;
         my_ur = U;
+        if (MODE == 2) {
+          const bool r_last = r_cur + 1u >= a.n_rows;
+          sub_lower(__uint_as_float(e_cur.pad), has, r_last, U, r_last ? 0.f : Lo, my_ll, my_lr);
+        }
       }
+    }
+    if (MODE == 4) {
+      // this lane's level-1 pool: the left item's exact score is the pool's
+      // minus the right item's, so it is accepted without its row when
+      // L_pool - U_right (rounded down) reaches rho, and otherwise tested from
+      // its row while U_pool - L_right (rounded up) does.  No right item: the
+      // left item is the whole pool.
+      // (its query's terms are read here: kept out of the loop's registers)
+      const bool has = mine && r_cur != kNoRow;
+      float Up = 0.f, Lp = 0.f, rho_4 = INFINITY;
+      if (mine) {
+        const SibPair ee = ins[bw * b + (uint32_t)lane];
+        Up = ee.U;
+        Lp = __uint_as_float(ee.pad);
+        rho_4 = a.rho[e_cur.q];
+      }
+      float U = 0.f, Lo = 0.f;
+      if (has) test_bounds<FMT>(a, my_acc, r_cur, a.qn1[e_cur.q], U, Lo);
+      const float Ul = has ? __fsub_ru(Up, r_cur + 1u >= a.n_rows ? 0.f : fmaxf(Lo, 0.f)) : Up;
+      const float Ll = has ? __fsub_rd(Lp, U) : Lp;
+      const bool al = mine && !a.no_accept && Ll >= rho_4;
+      m_e = __ballot_sync(FULL, al);
+      m_c = __ballot_sync(FULL, mine && !al && Ul >= rho_4);
     }
     if (PRE) {
       my_ul = my_acc;
@@ -1093,7 +1143,9 @@ __global__ void __launch_bounds__(32 * kRingWarps, 1)
       Pair right, left;
       right.q = pr.q; right.j = 2u * pr.j + 1u;
       left.q = pr.q; left.j = 2u * pr.j;
-      warp_append(a.res, a.res_count, a.res_cap, a.flags, (m_a >> lane) & 1u, right, right);
+      const bool ar = (m_a >> lane) & 1u, al = (m_e >> lane) & 1u;
+      warp_append(a.res, a.res_count, a.res_cap, a.flags, (ar ? 1u : 0u) + (al ? 1u : 0u),
+                  ar ? right : left, left);
       warp_append(a.rchk, a.rchk_count, a.rchk_cap, a.flags, (m_b >> lane) & 1u, right, right);
       if (FMT == GT_FP8 && m_d)
         warp_append(a.defer, a.defer_count, a.defer_cap, a.flags, (m_d >> lane) & 1u, right, right);
@@ -1109,7 +1161,7 @@ __global__ void __launch_bounds__(32 * kRingWarps, 1)
       const bool cl = (m_b >> lane) & 1u, cr = (m_d >> lane) & 1u;
       warp_append(a.rchk, a.rchk_count, a.rchk_cap, a.flags, (cl ? 1u : 0u) + (cr ? 1u : 0u), cl ? l : r, r);
     } else {
-      sub_emit<MODE == 3>(a, out_v, e_cur, m_a, m_b, my_ul, my_ur);
+      sub_emit<MODE == 3>(a, out_v, e_cur, m_a, m_b, my_ul, my_ur, my_ll, my_lr);
     }
     // next batch
     b += nw;
@@ -1351,8 +1403,13 @@ __global__ void __launch_bounds__(32 * kRingWarps, 1)
       // subtraction (kinds 0, 1): the left child's bound; the last row of a
       // level is not subtracted (an insert may have extended it since the
       // parent's bound was taken)
+      const bool r_last = r_cur + 1u >= L.n_rows;
       float Ul = e_cur.U;
-      if (kind != 2 && has) Ul = __fsub_ru(e_cur.U, r_cur + 1u >= L.n_rows ? 0.f : fmaxf(Lo, 0.f));
+      if (kind != 2 && has) Ul = __fsub_ru(e_cur.U, r_last ? 0.f : fmaxf(Lo, 0.f));
+      // the children's lower bounds (the right one's own, the left one's by
+      // subtraction)
+      float Ll = 0.f, Lr = 0.f;
+      if (kind != 2) sub_lower(__uint_as_float(e_cur.pad), has, r_last, U, r_last ? 0.f : Lo, Ll, Lr);
       if (kind == 0) {
         const bool kl = mine && Ul >= rho_l, kr = has && U >= rho_l;
         const uint32_t cntl = (kl ? 1u : 0u) + (kr ? 1u : 0u);
@@ -1360,9 +1417,8 @@ __global__ void __launch_bounds__(32 * kRingWarps, 1)
         uint32_t pos = dst_n + incl - cntl;
         SibPair x;
         x.q = e_cur.q;
-        x.pad = 0;
-        if (kl) { x.p = 2u * e_cur.p; x.U = Ul; dst[pos++] = x; }
-        if (kr) { x.p = 2u * e_cur.p + 1u; x.U = U; dst[pos++] = x; }
+        if (kl) { x.p = 2u * e_cur.p; x.U = Ul; x.pad = __float_as_uint(Ll); dst[pos++] = x; }
+        if (kr) { x.p = 2u * e_cur.p + 1u; x.U = U; x.pad = __float_as_uint(Lr); dst[pos++] = x; }
         dst_n += __shfl_sync(FULL, incl, 31);
       } else {
         // the gathered item: 0 pruned, 1 accepted, 2 FP64 recheck, 3 re-score
@@ -1374,9 +1430,12 @@ __global__ void __launch_bounds__(32 * kRingWarps, 1)
           else if (FMT == GT_FP8 && a.rows16 && a.defer) c = 4;
           else c = 3;
         }
+        // kind 1: the left item of a kept level-1 pool is accepted on its
+        // lower bound, or else goes to `left` for a direct test while its
+        // upper bound reaches rho
+        const bool al = kind == 1 && mine && !a.no_accept && Ll >= rho_l;
         if (kind == 1) {
-          // the left item of a kept level-1 pool goes to `left` for a direct test
-          const bool kl = mine && Ul >= rho_l;
+          const bool kl = mine && !al && Ul >= rho_l;
           const uint32_t incl = warp_incl_scan(kl ? 1u : 0u);
           if (kl) {
             Pair x;
@@ -1396,10 +1455,13 @@ __global__ void __launch_bounds__(32 * kRingWarps, 1)
                                                      nullptr, n_refine);
           if (lane == j) c = r;
         }
-        Pair it;
+        Pair it, il;
         it.q = e_cur.q;
         it.j = r_cur;
-        warp_append(a.res, a.res_count, a.res_cap, a.flags, c == 1 ? 1u : 0u, it, it);
+        il.q = e_cur.q;
+        il.j = 2u * e_cur.p;
+        warp_append(a.res, a.res_count, a.res_cap, a.flags, (c == 1 ? 1u : 0u) + (al ? 1u : 0u),
+                    c == 1 ? it : il, il);
         warp_append(a.rchk, a.rchk_count, a.rchk_cap, a.flags, c == 2 ? 1u : 0u, it, it);
         if (FMT == GT_FP8) {
           const uint32_t m_d = __ballot_sync(FULL, c == 4);
@@ -1636,16 +1698,29 @@ __global__ void k_root(Pair *out, uint32_t *count, uint32_t q0, uint32_t b) {
 // survivors of 32 queries at a time, so its list interleaves queries; grouped,
 // a warp of the level kernels keeps one query in registers for a whole run of
 // pairs, and the children it appends stay grouped for the next level.
+// The epilogue writes one query's survivors of a 32-pool chunk together, so
+// neighbouring entries mostly share a query: the lanes of a warp that hold
+// the same query combine their atomics (__match_any_sync), and the loops step
+// whole warps so that every lane takes part in each vote.
 template <typename E>
 __global__ void k_bucket_count(const E *in, const uint32_t *n_dev, uint32_t cap, uint32_t q0,
                                uint32_t b, int64_t *cnt, int *flags) {
   const uint32_t n = min(*n_dev, cap);
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const uint32_t k = in[i].q - q0;  // the micro-batch holds queries [q0, q0 + b)
-    if (k < b)
-      atomicAdd(reinterpret_cast<unsigned long long *>(&cnt[k]), 1ull);
-    else  // the list's count would then cover entries the scatter leaves out
-      atomicExch(&flags[kFlagStray], 1);
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t base = blockIdx.x * blockDim.x + threadIdx.x - lane; base < n; base += stride) {
+    const uint32_t i = base + lane;
+    uint32_t k = 0xffffffffu;
+    if (i < n) {
+      k = in[i].q - q0;  // the micro-batch holds queries [q0, q0 + b)
+      if (k >= b) {      // the list's count would then cover entries the scatter leaves out
+        atomicExch(&flags[kFlagStray], 1);
+        k = 0xffffffffu;
+      }
+    }
+    const uint32_t peers = __match_any_sync(FULL, k);
+    if (k != 0xffffffffu && lane == (uint32_t)(__ffs(peers) - 1))
+      atomicAdd(reinterpret_cast<unsigned long long *>(&cnt[k]), (unsigned long long)__popc(peers));
   }
 }
 
@@ -1653,13 +1728,25 @@ template <typename E>
 __global__ void k_bucket_scatter(const E *in, const uint32_t *n_dev, uint32_t cap, uint32_t q0,
                                  uint32_t b, const int64_t *off, int64_t *cursor, E *out) {
   const uint32_t n = min(*n_dev, cap);
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const E e = in[i];
-    const uint32_t k = e.q - q0;
-    if (k >= b) continue;
-    const unsigned long long slot =
-        atomicAdd(reinterpret_cast<unsigned long long *>(&cursor[k]), 1ull);
-    out[off[k] + (int64_t)slot] = e;
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t base = blockIdx.x * blockDim.x + threadIdx.x - lane; base < n; base += stride) {
+    const uint32_t i = base + lane;
+    E e;
+    uint32_t k = 0xffffffffu;
+    if (i < n) {
+      e = in[i];
+      k = e.q - q0;
+      if (k >= b) k = 0xffffffffu;
+    }
+    const uint32_t peers = __match_any_sync(FULL, k);
+    const int leader = __ffs(peers) - 1;
+    unsigned long long slot = 0;
+    if (k != 0xffffffffu && (int)lane == leader)
+      slot = atomicAdd(reinterpret_cast<unsigned long long *>(&cursor[k]),
+                       (unsigned long long)__popc(peers));
+    slot = __shfl_sync(FULL, slot, leader);
+    if (k != 0xffffffffu) out[off[k] + (int64_t)slot + __popc(peers & ((1u << lane) - 1u))] = e;
   }
 }
 
@@ -2188,6 +2275,7 @@ void launch_drain(gt_tree *t, int fmt, int cut, const SibPair *root, const uint3
   LevelArgs a;
   std::memset(&a, 0, sizeof(a));
   a.expire = t->expire_waits;
+  a.no_accept = t->split_sign ? 1 : 0;
   const int eb = entry_bytes(fmt);
   a.rows = fmt == GT_F32 ? reinterpret_cast<const uint8_t *>(t->rows32)
            : fmt == GT_BF16 ? reinterpret_cast<const uint8_t *>(t->rows16)
@@ -2525,6 +2613,7 @@ void launch_items_sub(gt_tree *t, int fmt, const SibPair *in, const uint32_t *in
   a.row_bytes = t->stride * eb;
   a.nvec = (int)((t->d * eb + 15) / 16);
   a.n_rows = (uint32_t)t->N;
+  a.no_accept = t->split_sign ? 1 : 0;
   a.qf32 = w.qf32;
   a.qstride = t->stride;
   a.qn1 = w.qn1;

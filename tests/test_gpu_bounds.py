@@ -78,8 +78,9 @@ def test_pair_bounds_hold_against_fp64(gt, d):
 
 
 def test_subtraction_bound_holds(gt):
-    # the left child's bound U_parent - max(L_right, 0) (rounded up by the
-    # kernels) is at or above the left child's exact score
+    # the left child's bounds: U_parent - max(L_right, 0) (rounded up by the
+    # kernels) is at or above its exact score, L_parent - U_right (rounded
+    # down) at or below it
     ds = synth.generate(synth.Workload("t", 8192, 256, 40, (0.8,), "uniform:10", seed=9),
                         screen=False)
     t = gt.Tree(ds.F)
@@ -93,9 +94,12 @@ def test_subtraction_bound_holds(gt):
         right[:, 1] = 2 * pp[:, 1] + 1
         left_exact = Sc[pp[:, 0], 2 * pp[:, 1]]
         for dtype in ("f32", "bf16", "fp8"):
-            Up = t.pair_bounds(h + 1, dtype, ds.Q, pp)[:, 1].astype(np.float64)
-            Lr = t.pair_bounds(h, dtype, ds.Q, right)[:, 2].astype(np.float64)
+            bp = t.pair_bounds(h + 1, dtype, ds.Q, pp).astype(np.float64)
+            br = t.pair_bounds(h, dtype, ds.Q, right).astype(np.float64)
+            Up, Lp = bp[:, 1], bp[:, 2]
+            Ur, Lr = br[:, 1], br[:, 2]
             assert np.all(Up - np.maximum(Lr, 0.0) >= left_exact), f"level {h} {dtype}"
+            assert np.all(Lp - Ur <= left_exact), f"level {h} {dtype}"
     t.close()
 
 

@@ -192,6 +192,45 @@ def test_insert_into_a_tail_sibling_keeps_the_left_bound(gt):
     t.close()
 
 
+@pytest.mark.parametrize("schedule", ["levels", "drain"])
+def test_insert_into_a_tail_pool_gives_no_lower_bound(gt, schedule):
+    # N0 = 3999: the last level-1 row holds item 3998 alone and is the right
+    # child of a level-2 pool that survives (item 3996 is a copy of the
+    # query).  After admission an insert puts another copy of the query
+    # (item 3999) into that row.  When the grown row is gathered, its lower
+    # bound covers the new item too, so it must not travel as the pool's
+    # lower bound: item 3998 (scoring below rho) would be accepted without
+    # its row as the pool's bound minus nothing (no right item in the view).
+    rng = np.random.default_rng(29)
+    d, n0 = 64, 3999
+    F = np.exp(3 * rng.standard_normal((n0 + 1, d)))
+    F /= np.linalg.norm(F, axis=1, keepdims=True)
+    F = F.astype(np.float32)
+    F[3996] = F[n0]
+    q = F[n0:n0 + 1].copy()
+    rho = np.array([0.9], np.float32)
+    ref = oracle.brute_force(F[:n0], q, rho, margin=0.0)
+    assert 3996 in ref.neighbours(0) and 3998 not in ref.neighbours(0)
+    assert float(F[3998].astype(np.float64) @ q[0].astype(np.float64)) < 0.8
+    t = gt.Tree(F[:n0], capacity=n0 + 16)
+    srv = gt.Server(t, dtype="bf16", cutover=3, schedule=schedule)
+    srv.submit(q, rho, np.array([5]))
+    srv.step()                           # admitted: the level-3 GEMM
+    if schedule == "levels":
+        srv.step()                       # level 2 (its right children gathered before the insert)
+    srv.insert(F[n0:n0 + 1])             # applied at the start of the next step
+    got = {}
+    for _ in range(6):
+        srv.step()
+        for tag, ids, snap in srv.poll():
+            got[tag] = (ids, snap)
+    srv.close()
+    ids, snap = got[5]
+    assert snap == n0
+    assert np.array_equal(ids, ref.neighbours(0))
+    t.close()
+
+
 def test_served_equals_alone(gt, stream_ds):
     ds = stream_ds
     n0 = 40_000

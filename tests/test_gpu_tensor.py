@@ -252,9 +252,12 @@ def test_subtraction_path_parity(gt, rho):
             lv_s, lv_d = sub.stats["level_tests"], direct.stats["level_tests"]
             above = sum(lv_s[1:cut])
             assert above <= 0.75 * sum(lv_d[1:cut]) + 16
-            # and at the items: a left item is gathered only when its bound
-            # (the pool's minus its right sibling's) reaches rho
-            assert lv_s[0] <= 0.9 * lv_d[0] + 16
+            # and at the items: a left item is gathered only when its upper
+            # bound (the pool's minus its right sibling's) reaches rho and its
+            # lower bound does not, so with BF16 or FP32 rows most left
+            # neighbours are accepted without their rows
+            frac = 0.9 if dtype == "fp8" else 0.7
+            assert lv_s[0] <= frac * lv_d[0] + 16, (dtype, cut, lv_s[0], lv_d[0])
     t.close()
 
 
