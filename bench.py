@@ -189,9 +189,11 @@ def _cpu_model() -> str:
     return f"{platform.processor() or platform.machine()} ({os.cpu_count()} cpus)"
 
 
-def _traffic_record(kernel: str):
+def _traffic_record(kernel: str, run_config: dict):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source (else None)."""
+    on the current kernel source and on this run's configuration (workload,
+    size, rho, row format, cutover: the mix of levels and the L2 reuse depend
+    on them), else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         rec = json.load(open(path)).get(kernel)
@@ -201,7 +203,11 @@ def _traffic_record(kernel: str):
         return None
     src = os.path.join(ROOT, "paper_2311_02573_gb300", "csrc", rec["source"])
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    return rec if sha == rec.get("source_sha") else None
+    if sha != rec.get("source_sha"):
+        return None
+    if any(run_config.get(k) != v for k, v in (rec.get("config") or {}).items()):
+        return None
+    return rec
 
 
 def reduce_max(value: float, dist=None) -> float:
@@ -750,13 +756,15 @@ def main():
     g_launches = max(1, st0["level_launches"] + st0["micro_batches"])
     gb = st0["gathered_bytes"]
     g_ach = gb / (gather_ms * 1e-3) / 1e9 if gather_ms > 0 else 0.0
-    tr = _traffic_record("gather_prefix" if pre else "gather")
+    run_cfg = {"workload": a.workload, "N": int(N), "queries": int(B), "rho": a.rho,
+               "dtype": a.dtype, "cutover": st0["cutover"]}
+    tr = _traffic_record("gather_prefix" if pre else "gather", run_cfg)
     # Rows of popular pools are read by many queries and partly served from L2,
     # so the algorithmic row bytes per second can exceed the copy peak.  The
     # fraction is therefore taken on DRAM bytes (the algorithmic bytes times
-    # the DRAM/algorithmic ratio of an ncu capture of the same kernels on a
-    # small case, recorded with its command in profiles/traffic.json); the
-    # algorithmic rate is reported beside it.
+    # the DRAM/algorithmic ratio of a one-pass ncu capture of the same kernels
+    # on the same configuration, recorded with its command in
+    # profiles/traffic.json); the algorithmic rate is reported beside it.
     ratio = tr["dram_bytes_per_algorithmic_byte"] if tr else None
     traffic = ratio * gb / g_launches if ratio else None
     g_dram = g_ach * ratio if ratio else None
@@ -768,7 +776,8 @@ def main():
                    "frac": round((g_dram if ratio else g_ach) / peaks["hbm_gbs"], 4),
                    "basis": "DRAM bytes (algorithmic bytes x the DRAM/algorithmic ratio of "
                             f"{tr.get('case', 'an ncu capture')}) per CUDA-event second" if ratio else
-                            "algorithmic bytes (no DRAM record for the current kernel source)",
+                            "algorithmic bytes (no DRAM record for the current kernel source "
+                            "and this configuration)",
                    "achieved_algorithmic": round(g_ach, 1),
                    "frac_algorithmic": round(g_ach / peaks["hbm_gbs"], 4),
                    "dram_per_algorithmic_byte": ratio,
@@ -784,7 +793,7 @@ def main():
         n_l = max(1, st0["micro_batches"])
         ach = flops / (km["dense"] * 1e-3) / 1e12
         peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
-        trd = _traffic_record("k_dense")
+        trd = _traffic_record("k_dense", run_cfg)
         roof_dense = {"kernel": "k_dense (tcgen05 cutover GEMM)", "bound": "tensor",
                       "achieved": round(ach, 1), "peak": peak, "unit": "TFLOP/s",
                       "frac": round(ach / peak, 4),

@@ -26,3 +26,20 @@ def test_reference_arm_json_line():
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+
+
+def test_traffic_record_needs_the_same_source_and_configuration():
+    # the DRAM/algorithmic ratio of a capture applies only to the kernel source
+    # and the configuration it was taken on
+    sys.path.insert(0, ROOT)
+    import bench
+    rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    for kernel in ("gather", "gather_prefix", "k_dense"):
+        cfg = dict(rec[kernel]["config"])
+        got = bench._traffic_record(kernel, cfg)
+        import hashlib
+        src = os.path.join(ROOT, "paper_2311_02573_gb300", "csrc", rec[kernel]["source"])
+        current = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] == rec[kernel]["source_sha"]
+        assert (got is not None) == current
+        for key, other in (("rho", 0.9), ("dtype", "f32"), ("cutover", 4), ("N", 20_000)):
+            assert bench._traffic_record(kernel, dict(cfg, **{key: other})) is None
