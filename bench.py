@@ -792,14 +792,19 @@ def main():
         flops = 2.0 * st0["dense_tests"] * d               # per step (one launch per micro-batch)
         n_l = max(1, st0["micro_batches"])
         ach = flops / (km["dense"] * 1e-3) / 1e12
-        peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+        # The step is a few milliseconds with idle gaps (the L2 flush) between
+        # steps, and the SM clock stays at its maximum through the timed
+        # region (the clock record), so the GEMM is compared with the burst
+        # figure; the seconds-long power-capped figure is reported beside it.
+        peak = peaks["bf16_tflops"]
+        sus = peaks.get("bf16_tflops_sustained")
         trd = _traffic_record("k_dense", run_cfg)
         roof_dense = {"kernel": "k_dense (tcgen05 cutover GEMM)", "bound": "tensor",
                       "achieved": round(ach, 1), "peak": peak, "unit": "TFLOP/s",
                       "frac": round(ach / peak, 4),
-                      "frac_of_burst": round(ach / peaks["bf16_tflops"], 4),
-                      "peak_source": f"bf16_tflops_sustained of {peaks_src} (timed inside a step); "
-                                     f"frac_of_burst against bf16_tflops",
+                      "frac_of_sustained": round(ach / sus, 4) if sus else None,
+                      "peak_source": f"bf16_tflops (burst) of {peaks_src}; frac_of_sustained "
+                                     f"against bf16_tflops_sustained (seconds-long, power-capped)",
                       "algorithmic_flops_per_launch": flops / n_l,
                       "avg_launch_ms": km["dense"] / n_l,
                       "traffic": (trd["dram_bytes_per_flop"] * flops / n_l) if trd else None,
