@@ -951,63 +951,139 @@ __global__ void __launch_bounds__(32 * kRingWarps, 1)
     const float rho_l = (PER_LANE && mine) ? a.rho[e_cur.q] : INFINITY;
     const float sc_l =
         (FMT == GT_FP8 && PER_LANE && !PRE && mine && r_cur != kNoRow) ? a.scales[r_cur] : 1.f;
-    for (uint32_t i = 0; i < len_cur; ++i, ++t) {
-      const uint32_t q = __shfl_sync(FULL, e_cur.q, i);
-      const uint32_t rowi = __shfl_sync(FULL, r_cur, i);
-      const bool has = rowi != kNoRow;
-      if (q != cur_q) load_query(q);
-      const bool good = ring_wait(full0 + 8u * k, ph, a.expire ? 0ull : kRingWaitNs);
-      if (!__all_sync(FULL, good)) {
-        ok = false;
-        break;
+    // refill slot kk with the row of stream position tt + depth (tt is the
+    // position of this batch's pair ii)
+    auto refill = [&](uint32_t kk, uint32_t tt, uint32_t ii) {
+      const uint32_t tn = tt + depth;
+      const uint32_t in_batch = ii + depth;  // position relative to this batch
+      uint32_t row = kNoRow;
+      bool have = false;
+      if (in_batch < len_cur) {
+        row = __shfl_sync(FULL, r_cur, in_batch);
+        have = true;
+      } else if (len_cur == bw && in_batch - bw < len_nxt) {
+        row = __shfl_sync(FULL, r_nxt, in_batch - bw);
+        have = true;
       }
-      uint4 w[KV];
-      const uint4 *rowp = reinterpret_cast<const uint4 *>(gslot0 + (size_t)k * slot_bytes);
+      if (have && tn == t_issued) {
+        issue(kk, row);
+        ++t_issued;
+      }
+    };
+    // BF16 rows at the pool levels: two pairs per pass, both slots waited,
+    // one proxy fence and one warp barrier, both refills, and the two warp
+    // sums folded into one butterfly (after the first exchange lanes 0-15
+    // carry pair i's sum and lanes 16-31 pair i+1's; each half then ends with
+    // exactly warp_sum's value).  A pass's second slot is the one after k
+    // (slot 0 of the next phase when k is the last; the depth may be odd).
+    // (2% faster for BF16 rows of up to 1024 entries; slower for FP8 and FP32
+    // rows, and more registers than wider rows have, so those keep one pair
+    // per pass.)
+    constexpr bool TWO = PER_LANE && FMT == GT_BF16 && KV <= 4;
+    if constexpr (TWO) {
+      for (uint32_t i = 0; i < len_cur; i += 2, t += 2) {
+        const bool two = i + 1u < len_cur;
+        const uint32_t q0 = __shfl_sync(FULL, e_cur.q, i);
+        const uint32_t row0 = __shfl_sync(FULL, r_cur, i);
+        const uint32_t q1 = __shfl_sync(FULL, e_cur.q, two ? i + 1u : i);
+        const uint32_t row1 = __shfl_sync(FULL, r_cur, two ? i + 1u : i);
+        const bool wrap = k + 1u == depth;
+        const uint32_t k2 = wrap ? 0u : k + 1u, ph2 = wrap ? (ph ^ 1u) : ph;
+        if (q0 != cur_q) load_query(q0);
+        bool good = ring_wait(full0 + 8u * k, ph, a.expire ? 0ull : kRingWaitNs);
+        if (two && good) good = ring_wait(full0 + 8u * k2, ph2, kRingWaitNs);
+        if (!__all_sync(FULL, good)) {
+          ok = false;
+          break;
+        }
+        uint4 w[KV];
+        {
+          const uint4 *rowp = reinterpret_cast<const uint4 *>(gslot0 + (size_t)k * slot_bytes);
+          const bool has = row0 != kNoRow;
 #pragma unroll
-      for (int kk = 0; kk < KV; ++kk) {
-        const int v = lane + 32 * kk;
-        w[kk] = (has && v < a.nvec) ? rowp[v] : make_uint4(0u, 0u, 0u, 0u);
-      }
-      float acc = row_dot<FMT, KV, false>(w, qreg, nullptr, a.nvec);
-      // the slot's next contents arrive through the async proxy: order this
-      // warp's reads of it before the copy that refills it
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncwarp();
-      // refill slot k with the row of pair t + depth of the stream
-      {
-        const uint32_t tn = t + depth;
-        const uint32_t in_batch = i + depth;  // position relative to this batch
-        uint32_t row = kNoRow;
-        bool have = false;
-        if (in_batch < len_cur) {
-          row = __shfl_sync(FULL, r_cur, in_batch);
-          have = true;
-        } else if (len_cur == bw && in_batch - bw < len_nxt) {
-          row = __shfl_sync(FULL, r_nxt, in_batch - bw);
-          have = true;
+          for (int kk = 0; kk < KV; ++kk) {
+            const int v = lane + 32 * kk;
+            w[kk] = (has && v < a.nvec) ? rowp[v] : make_uint4(0u, 0u, 0u, 0u);
+          }
         }
-        if (have && tn == t_issued) {
-          issue(k, row);
-          ++t_issued;
+        const float acc0 = row_dot<FMT, KV, false>(w, qreg, nullptr, a.nvec);
+        float acc1 = 0.f;
+        if (two) {
+          if (q1 != cur_q) load_query(q1);  // the pass straddles a query boundary
+          const uint4 *rowp = reinterpret_cast<const uint4 *>(gslot0 + (size_t)k2 * slot_bytes);
+          const bool has = row1 != kNoRow;
+#pragma unroll
+          for (int kk = 0; kk < KV; ++kk) {
+            const int v = lane + 32 * kk;
+            w[kk] = (has && v < a.nvec) ? rowp[v] : make_uint4(0u, 0u, 0u, 0u);
+          }
+          acc1 = row_dot<FMT, KV, false>(w, qreg, nullptr, a.nvec);
         }
+        // the slots' next contents arrive through the async proxy: order this
+        // warp's reads of them before the copies that refill them
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        refill(k, t, i);
+        k = k2;
+        ph = ph2;
+        if (two) {
+          refill(k, t + 1u, i + 1u);
+          if (++k == depth) {
+            k = 0;
+            ph ^= 1u;
+          }
+        }
+        const bool hi = (lane & 16) != 0;
+        float keep = hi ? acc1 : acc0;
+        keep += __shfl_xor_sync(FULL, hi ? acc0 : acc1, 16);
+#pragma unroll
+        for (int off = 8; off > 0; off >>= 1) keep += __shfl_xor_sync(FULL, keep, off);
+        const float s0 = __shfl_sync(FULL, keep, 0), s1 = __shfl_sync(FULL, keep, 16);
+        if ((uint32_t)lane == i) my_acc = s0;
+        if (two && (uint32_t)lane == i + 1u) my_acc = s1;
       }
-      if (++k == depth) {
-        k = 0;
-        ph ^= 1u;
-      }
-      acc = warp_sum(acc);
-      if (MODE == 1) {
-        decide<FMT, KV, true, false>(a, acc, rowi, qn1, rho, qreg, nullptr, (int)i, m_a, m_b, m_d,
-                                     n_refine);
-      } else if (MODE == 4) {
-        // the right item decided here; its score kept by lane i, which bounds
-        // the left item after the batch
-        if (has)
-          decide<FMT, KV, true, false>(a, acc, rowi, qn1, rho, qreg, nullptr, (int)i, m_a, m_b, m_d,
-                                       n_refine);
-        if ((uint32_t)lane == i) my_acc = acc;
-      } else if ((uint32_t)lane == i) {
-        my_acc = acc;
+    } else {
+      for (uint32_t i = 0; i < len_cur; ++i, ++t) {
+        const uint32_t q = __shfl_sync(FULL, e_cur.q, i);
+        const uint32_t rowi = __shfl_sync(FULL, r_cur, i);
+        const bool has = rowi != kNoRow;
+        if (q != cur_q) load_query(q);
+        const bool good = ring_wait(full0 + 8u * k, ph, a.expire ? 0ull : kRingWaitNs);
+        if (!__all_sync(FULL, good)) {
+          ok = false;
+          break;
+        }
+        uint4 w[KV];
+        const uint4 *rowp = reinterpret_cast<const uint4 *>(gslot0 + (size_t)k * slot_bytes);
+#pragma unroll
+        for (int kk = 0; kk < KV; ++kk) {
+          const int v = lane + 32 * kk;
+          w[kk] = (has && v < a.nvec) ? rowp[v] : make_uint4(0u, 0u, 0u, 0u);
+        }
+        float acc = row_dot<FMT, KV, false>(w, qreg, nullptr, a.nvec);
+        // the slot's next contents arrive through the async proxy: order this
+        // warp's reads of it before the copy that refills it
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        refill(k, t, i);
+        if (++k == depth) {
+          k = 0;
+          ph ^= 1u;
+        }
+        acc = warp_sum(acc);
+        if (MODE == 1) {
+          decide<FMT, KV, true, false>(a, acc, rowi, qn1, rho, qreg, nullptr, (int)i, m_a, m_b,
+                                       m_d, n_refine);
+        } else if (MODE == 4) {
+          // MODE 4: the right item decided here; its score kept by lane i,
+          // which bounds the left item after the batch
+          if (has)
+            decide<FMT, KV, true, false>(a, acc, rowi, qn1, rho, qreg, nullptr, (int)i, m_a, m_b,
+                                         m_d, n_refine);
+          if ((uint32_t)lane == i) my_acc = acc;
+        } else if ((uint32_t)lane == i) {
+          my_acc = acc;
+        }
       }
     }
     if (!ok) break;
@@ -2705,7 +2781,9 @@ void launch_csr_into(gt_tree *t, const Pair *res, uint32_t n, const uint32_t *n_
 void launch_bucket(gt_tree *t, bool sib, const void *in, void *out, const uint32_t *n_dev,
                    uint32_t cap, int64_t q0, int64_t b, cudaStream_t s) {
   Workspace &w = t->ws;
-  const int blocks = t->sm_count * 4;
+  // a full SM's worth of warps each: the passes are bound by load and
+  // atomic latency, not by bandwidth
+  const int blocks = t->sm_count * 8;
   const uint32_t uq0 = (uint32_t)q0, ub = (uint32_t)b;
   cudaMemsetAsync(w.bcnt, 0, (size_t)(b + 1) * sizeof(int64_t), s);
   if (sib)

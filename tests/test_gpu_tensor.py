@@ -313,11 +313,12 @@ def test_ring_gather_tiny_lists(gt):
     t.close()
 
 
-@pytest.mark.parametrize("d", [16, 100, 513, 1000, 1024, 1040])
+@pytest.mark.parametrize("d", [16, 100, 513, 600, 800, 1000, 1024, 1040])
 def test_ring_gather_widths(gt, d):
     # the ring-fed gather over row widths: rows of one to eight 16-byte
     # vectors per lane, the widest narrow rows (1024) and the first wide ones
-    # (1040); frontier, leaves, subtraction levels and items, and retries
+    # (1040), and BF16 rows whose ring depth is odd (600, 800: 7 and 5 slots
+    # per warp); frontier, leaves, subtraction levels and items, and retries
     ds = synth.generate(synth.Workload("t", 12_000, d, 90, (0.85,), "uniform:8", seed=d))
     r = ds.rho_for(0.85)
     ref = oracle.brute_force(ds.F, ds.Q, r)
@@ -328,6 +329,11 @@ def test_ring_gather_widths(gt, d):
             same_sets(t.query(ds.Q, r, dtype=dtype, cutover=cut, subtract=sub), ref)
     same_sets(t.query(ds.Q, r, dtype="bf16", cutover=3, max_batch=7, scratch_bytes=1 << 19), ref)
     t.close()
+    if d in (600, 800, 1000):
+        # the prefix layout's splits take the same ring
+        tp = gt.Tree(ds.F, layout="prefix", prefix_level=3)
+        same_sets(tp.query(ds.Q, r, dtype="bf16"), ref)
+        tp.close()
 
 
 @pytest.mark.parametrize("inflight", [0, 4, 16])
