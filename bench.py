@@ -289,7 +289,7 @@ def serve_run(gt, tree, Q, rhos, rate, n_req, dtype, inserts=None, insert_frac=0
             "p99_ms": round(float(np.percentile(l, 99)), 3),
             "steps": st["steps"], "mean_group": round(st["admitted"] / max(1, st["steps"]), 1),
             "cutover": st["cutover"], "launches": st["launches"],
-            "schedule": {1: "levels", 2: "drain"}.get(st["schedule"], st["schedule"])}
+            "schedule": {1: "levels", 2: "drain", 3: "immediate"}.get(st["schedule"], st["schedule"])}
 
 
 
@@ -991,11 +991,12 @@ def main():
             n_req = int(min(200_000, max(20_000, r * 0.4))) if r > 0 else 100_000
             serving.append(serve_run(gt, tree, Q, rhos, r, n_req, a.dtype, inserts=extra))
         if not pre and a.cutover == -1 and tune is not None:
-            # the server's two schedules at 50k q/s offered, back to back: one
-            # launch per level per step, or each step draining the previous
-            # step's group in one persistent launch
+            # the server's three schedules at 50k q/s offered, back to back:
+            # one launch per level per step; each step draining the previous
+            # step's group in one persistent launch; or each step answering
+            # the group it admits (GEMM, then that launch)
             serving_schedules = {}
-            for sched in ("levels", "drain"):
+            for sched in ("levels", "drain", "immediate"):
                 serving_schedules[sched] = serve_run(gt, tree, Q, rhos, 50000.0, 20000, a.dtype,
                                                      inserts=extra, seed=5, schedule=sched)
             serving.append({"schedules_at_50k": serving_schedules})

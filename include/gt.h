@@ -398,14 +398,14 @@ gt_status gt_query_static(gt_tree *t, const float *Q, int64_t B, const float *rh
 
 /* ---- Serving: continuous batching over one tree ------------------------
  * A request loop for range queries (Sec. 2) arriving over time, with
- * streaming inserts (Sec. 4) interleaved.  Every gt_server_step advances all
- * query groups in flight by one tree level, completes the group that reached
- * the items, applies queued inserts, and admits a new group from the arrival
- * queue (bounded by free query slots and the frontier memory budget) whose
- * dense cutover GEMM runs in the same step.  Groups at different levels share
- * each step's kernels, so later arrivals overlap earlier ones on the device.
- * Each group answers for the tree as it was when the group was admitted:
- * {i < N_admit : q.f_i >= rho}, the same set it gets alone. */
+ * streaming inserts (Sec. 4) interleaved.  Every gt_server_step applies
+ * queued inserts, admits a new group from the arrival queue (bounded by free
+ * query slots and the frontier memory budget) whose dense cutover GEMM runs
+ * in that step, moves the groups in flight below the cutover as the schedule
+ * says (gt_server_schedule), and completes the groups that reach a decision.
+ * A request that arrives while others are on the device joins at the next
+ * step.  Each group answers for the tree as it was when the group was
+ * admitted: {i < N_admit : q.f_i >= rho}, the same set it gets alone. */
 typedef struct gt_server gt_server;
 
 typedef struct gt_server_opts {
@@ -422,23 +422,32 @@ typedef struct gt_server_opts {
 } gt_server_opts;
 
 /* Schedules of the server.
- *   GT_SCHEDULE_LEVELS  one level per step: every step launches, for each
- *                       group in flight, the kernel of the level it is at, so
- *                       a group finishes c + 1 steps after admission and up
- *                       to c + 1 groups share each step.
- *   GT_SCHEDULE_DRAIN   each step drains the group admitted the step before
- *                       in one persistent launch (every level below the
- *                       cutover and its items, the warps working through the
- *                       GEMM's list as a shared queue) while it admits the
- *                       next group: two groups share each step and a group
- *                       finishes one step after admission.  Needs the
- *                       subtraction path (sum pools, cutover 2 to 5).
- *   GT_SCHEDULE_AUTO    GT_SCHEDULE_DRAIN where it applies, else
- *                       GT_SCHEDULE_LEVELS. */
+ *   GT_SCHEDULE_LEVELS     one level per step: every step launches, for each
+ *                          group in flight, the kernel of the level it is at,
+ *                          so a group finishes c + 1 steps after admission and
+ *                          up to c + 1 groups share each step.
+ *   GT_SCHEDULE_DRAIN      each step drains the group admitted the step before
+ *                          in one persistent launch (every level below the
+ *                          cutover and its items, the warps working through
+ *                          the GEMM's list as a shared queue) while it admits
+ *                          the next group: two groups share each step and a
+ *                          group finishes one step after admission.
+ *   GT_SCHEDULE_IMMEDIATE  each step admits a group and answers it in the
+ *                          same step (its GEMM, the same persistent launch,
+ *                          the recheck and its neighbour lists): a request is
+ *                          answered at the end of the first step that starts
+ *                          after it arrives, and no group stays in flight
+ *                          between steps.  A group whose lists overflow is
+ *                          answered again, smaller, by a later step.
+ *   GT_SCHEDULE_AUTO       GT_SCHEDULE_IMMEDIATE where it applies, else
+ *                          GT_SCHEDULE_LEVELS.
+ * DRAIN and IMMEDIATE need the subtraction path (sum pools, cutover 2 to 5,
+ * tree layout); GT_EINVAL otherwise. */
 typedef enum gt_server_schedule {
   GT_SCHEDULE_AUTO = 0,
   GT_SCHEDULE_LEVELS = 1,
-  GT_SCHEDULE_DRAIN = 2
+  GT_SCHEDULE_DRAIN = 2,
+  GT_SCHEDULE_IMMEDIATE = 3
 } gt_server_schedule;
 
 typedef struct gt_server_stats {
@@ -446,7 +455,7 @@ typedef struct gt_server_stats {
   int64_t steps, launches, retries, rechecks, refines;
   int64_t gathered_tests, dense_tests;
   int64_t cutover, max_group;
-  int64_t schedule;      /* the gt_server_schedule in use (LEVELS or DRAIN) */
+  int64_t schedule;      /* the gt_server_schedule in use (LEVELS, DRAIN or IMMEDIATE) */
   double busy_seconds;   /* host wall time spent inside gt_server_step */
 } gt_server_stats;
 

@@ -15,7 +15,10 @@
 //      free query slots and the frontier memory budget allow, runs its dense
 //      GEMM and groups the survivors by query.
 // Groups therefore overlap on the device: a request that arrives while others
-// are in flight joins at the next step.  Every level's list holds exactly
+// are in flight joins at the next step.  (That is the one-level-per-step
+// schedule; the drain schedule takes a group through every level below the
+// cutover in the step after its admission, and the immediate schedule in the
+// step that admits it: gt_server_schedule.)  Every level's list holds exactly
 // one group.  Each group records the tree size at admission and traverses
 // that snapshot (later inserts only raise pool sums, so the bounds stay
 // valid), so a query's answer is the same alone and in the mix.
@@ -78,6 +81,10 @@ struct gt_server {
   // next, so each step drains the group admitted the step before while it
   // admits the next one
   bool drain = false;
+  // GT_SCHEDULE_IMMEDIATE: each step admits a group and answers it at once
+  // (GEMM, the same persistent launch, recheck, CSR), so no group is left in
+  // flight between steps
+  bool immediate = false;
   void *drain_buf = nullptr;
   int64_t drain_cap = 0;
   // per level two lists (parity), results, rechecks, counters, flags
@@ -235,6 +242,158 @@ double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
+// Queued inserts, in one batch, before any kernel of the step.
+gt_status apply_inserts(gt_server *S) {
+  if (S->ins_n == 0) return GT_OK;
+  GT_CUDA(cudaMemcpyAsync(S->ins_d, S->ins_h, (size_t)S->ins_n * S->t->d_in * sizeof(float),
+                          cudaMemcpyHostToDevice, S->s));
+  gt_status st = gt_insert(S->t, S->ins_d, S->ins_n, S->s);
+  if (st != GT_OK) return st;
+  S->st.inserted += S->ins_n;
+  S->ins_n = 0;
+  return GT_OK;
+}
+
+// Queries to admit this step: the queue's head, at most max_group, and what
+// the frontier budget holds (a group's level-(c-1) entries at most double per
+// level below: a list's entries / 2^(c-1), with a 25% margin).
+int64_t admit_count(const gt_server *S, int64_t list_room) {
+  int64_t b = std::min<int64_t>(S->ring_size, S->max_group);
+  if (b > 0 && S->est_pairs_per_query > 0) {
+    const int64_t fit = (int64_t)((double)list_room / (1.25 * S->est_pairs_per_query));
+    b = std::max<int64_t>(1, std::min(b, fit));
+  }
+  return b;
+}
+
+// The oldest b queued queries (one or two contiguous pieces of the pinned
+// ring) into the staging buffer, then into query slots [s0, s0 + b).
+gt_status stage_queries(gt_server *S, int64_t b, int64_t s0) {
+  cudaStream_t s = S->s;
+  const int d = S->t->d_in;
+  const int64_t k0 = S->ring_head, n1 = std::min(b, S->ring_cap - k0), n2 = b - n1;
+  GT_CUDA(cudaMemcpyAsync(S->stage, S->ring_q + k0 * d, (size_t)n1 * d * sizeof(float),
+                          cudaMemcpyHostToDevice, s));
+  GT_CUDA(cudaMemcpyAsync(S->stage + (size_t)b * d, S->ring_rho + k0, (size_t)n1 * sizeof(float),
+                          cudaMemcpyHostToDevice, s));
+  if (n2 > 0) {
+    GT_CUDA(cudaMemcpyAsync(S->stage + (size_t)n1 * d, S->ring_q, (size_t)n2 * d * sizeof(float),
+                            cudaMemcpyHostToDevice, s));
+    GT_CUDA(cudaMemcpyAsync(S->stage + (size_t)b * d + n1, S->ring_rho, (size_t)n2 * sizeof(float),
+                            cudaMemcpyHostToDevice, s));
+  }
+  gt_tree vq = view_of(S, S->t->N, s0);
+  launch_prep_queries(&vq, S->stage, S->stage + (size_t)b * d, b, s);
+  return GT_OK;
+}
+
+// The flags every step checks after its synchronize.
+gt_status step_flags(gt_server *S, const uint32_t *hc) {
+  if (hc[64 + kFlagTimeout]) return set_error(GT_ETIMEOUT, "a bounded device wait expired");
+  if (hc[64 + kFlagDomain])
+    return set_error(GT_EDOMAIN, S->t->split_sign ? "a query has a non-finite entry"
+                                                  : "a query has a negative or non-finite entry");
+  return GT_OK;
+}
+
+// GT_SCHEDULE_IMMEDIATE: one step admits a group from the queue's head and
+// answers it: the dense GEMM at the cutover, its survivors grouped by query,
+// one persistent launch for every level below and the items (k_drain), the
+// FP64 recheck and the CSR, then one synchronize.  A request waits for the
+// next step to start and is answered when that step ends.  A group whose
+// GEMM list or result list overflowed is answered again, smaller, in a later
+// step (its queries stay at the queue's head); nothing else carries over
+// between steps.
+gt_status step_immediate(gt_server *S, int64_t *in_flight) {
+  gt_tree *t = S->t;
+  cudaStream_t s = S->s;
+  const double t0 = now_s();
+  gt_status st = apply_inserts(S);
+  if (st != GT_OK) return st;
+  const int p = (int)(S->step_no & 1), np = 1 - p;
+  const int cut = S->cut;
+  const int64_t room = list_entries(S);
+  const int64_t b = admit_count(S, room);
+  int64_t launches = 0;
+  if (b > 0) {
+    k_step_reset<<<1, 64, 0, s>>>(S->counters, np, cut);
+    const int64_t s0 = 0;  // one group at a time: the first group's slots
+    st = stage_queries(S, b, s0);
+    if (st != GT_OK) return st;
+    gt_tree v = view_of(S, t->N, 0);
+    v.ring_batch = ring_batch_for(b);
+    uint32_t *gemm_count = S->counters + 2 * (cut - 1) + np;
+    st = launch_dense(&v, cut, 3, s0, b, S->gemm_out, gemm_count, s);
+    if (st != GT_OK) return st;
+    launch_bucket(&v, true, S->gemm_out, S->lists[cut - 1][np], gemm_count, (uint32_t)room, s0, b, s);
+    launch_drain(&v, S->fmt, cut, reinterpret_cast<const SibPair *>(S->lists[cut - 1][np]), gemm_count,
+                 s, S->counters + kDrainCounts, S->counters + kDrainCounts + 8);
+    launch_recheck(&v, 0, s);
+    GT_CUDA(cudaMemsetAsync(S->cnt + s0, 0, (size_t)(b + 1) * sizeof(int64_t), s));
+    launch_csr_into(&v, S->res, (uint32_t)S->res_cap, S->counters + kMaxLevels, s0, b, S->cnt, S->off,
+                    S->ids, S->counters + kCsrListSlot, s);
+    GT_CUDA(cudaMemcpyAsync(S->hoff, S->off + s0, (size_t)(b + 1) * sizeof(int64_t),
+                            cudaMemcpyDeviceToHost, s));
+    const int64_t ids_pre = std::min<int64_t>(S->ids_guess, S->hids_cap);
+    GT_CUDA(cudaMemcpyAsync(S->hids, S->ids, (size_t)ids_pre * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    GT_CUDA(cudaGetLastError());
+    GT_CUDA(cudaMemcpyAsync(S->hcounters, S->counters, 128 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    GT_CUDA(cudaStreamSynchronize(s));
+    launches += 16;  // prep, thresholds, GEMM, 4 grouping, drain, recheck, 6 CSR, reset
+    const uint32_t *hc = S->hcounters;
+    st = step_flags(S, hc);
+    if (st != GT_OK) return st;
+    if (hc[64 + kFlagStray])
+      return set_error(GT_ECUDA, "internal error: a list entry names a query or row outside its "
+                                 "buffers; step " + std::to_string(S->step_no));
+    const uint32_t gemm_pairs = hc[2 * (cut - 1) + np];
+    const double per_q = (double)gemm_pairs / (double)b;
+    if (hc[64 + kFlagOverflow] || gemm_pairs > (uint32_t)room) {
+      // the group did not fit (its GEMM list, or its results or rechecks):
+      // its answers are dropped and its queries stay queued for a smaller
+      // group
+      if (b == 1)
+        return set_error(GT_EOVERFLOW, "one query's frontier or neighbours exceed the server's budget");
+      S->max_group = std::max<int64_t>(1, b / 2);
+      S->est_pairs_per_query = std::max(S->est_pairs_per_query, per_q);
+      ++S->st.retries;
+    } else {
+      const int64_t first = S->hoff[0], n_ids = S->hoff[b] - first;
+      if (first + n_ids > ids_pre) {
+        GT_CUDA(cudaMemcpyAsync(S->hids + ids_pre, S->ids + ids_pre,
+                                (size_t)(first + n_ids - ids_pre) * sizeof(int32_t),
+                                cudaMemcpyDeviceToHost, s));
+        GT_CUDA(cudaStreamSynchronize(s));
+      }
+      S->ids_guess = std::max<int64_t>(4096, 2 * (first + n_ids));
+      const size_t base_ids = S->done_ids.size();
+      S->done_ids.insert(S->done_ids.end(), S->hids + first, S->hids + first + n_ids);
+      for (int64_t i = 0; i < b; ++i) {
+        S->done_tag.push_back(S->ring_tag[(size_t)((S->ring_head + i) % S->ring_cap)]);
+        S->done_snap.push_back(t->N);
+        S->done_off.push_back((int64_t)base_ids + (S->hoff[i + 1] - first));
+      }
+      S->ring_head = (S->ring_head + b) % S->ring_cap;
+      S->ring_size -= b;
+      S->est_pairs_per_query = std::max(S->est_pairs_per_query * 0.9, per_q);
+      S->st.admitted += b;
+      S->st.completed += b;
+      S->st.rechecks += hc[kMaxLevels + 1];
+      S->st.refines += hc[kMaxLevels + 2];
+      S->st.dense_tests += b * level_rows(t->N, cut);
+      S->st.gathered_tests += gemm_pairs;
+      for (int h = 0; h + 1 < cut; ++h) S->st.gathered_tests += hc[kDrainCounts + h];
+      S->st.gathered_tests += hc[kDrainCounts + 8];
+    }
+  }
+  S->step_no += 1;
+  S->st.steps += 1;
+  S->st.launches += launches;
+  S->st.busy_seconds += now_s() - t0;
+  if (in_flight) *in_flight = 0;
+  return GT_OK;
+}
+
 }  // namespace
 }  // namespace gt
 
@@ -273,17 +432,18 @@ gt_status gt_server_create(gt_tree *t, const gt_server_opts *opts, gt_server **o
   S->items_sub = !pre && S->sub && items_sub_available(t, o.dtype);
   // one persistent launch for the levels below the cutover, where it applies
   // (unless the caller asked for one level per step)
-  if (o.schedule < GT_SCHEDULE_AUTO || o.schedule > GT_SCHEDULE_DRAIN) {
+  if (o.schedule < GT_SCHEDULE_AUTO || o.schedule > GT_SCHEDULE_IMMEDIATE) {
     delete S;
     return set_error(GT_EINVAL, "unknown schedule");
   }
   S->drain = o.schedule != GT_SCHEDULE_LEVELS && !pre && S->items_sub &&
              drain_available(t, o.dtype, cut);
-  if (o.schedule == GT_SCHEDULE_DRAIN && !S->drain) {
+  if ((o.schedule == GT_SCHEDULE_DRAIN || o.schedule == GT_SCHEDULE_IMMEDIATE) && !S->drain) {
     delete S;
-    return set_error(GT_EINVAL, "the drain schedule needs the subtraction path of a sum-pooled "
-                                "tree with the cutover at level 2 to 5");
+    return set_error(GT_EINVAL, "the drain and immediate schedules need the subtraction path of "
+                                "a sum-pooled tree with the cutover at level 2 to 5");
   }
+  S->immediate = S->drain && o.schedule != GT_SCHEDULE_DRAIN;
   S->max_group = o.max_group > 0 ? o.max_group : 4096;
   S->group_stride = S->max_group;
   S->queue_cap = o.queue_capacity;
@@ -377,18 +537,13 @@ gt_status gt_server_insert(gt_server *S, const float *f, int64_t n) {
 gt_status gt_server_step(gt_server *S, int64_t *in_flight) {
   if (!S) return set_error(GT_EINVAL, "null server");
   TraceRange trace("gt_server_step");
+  if (S->immediate) return step_immediate(S, in_flight);
   gt_tree *t = S->t;
   cudaStream_t s = S->s;
   const double t0 = now_s();
   // 1. queued inserts, in one batch, before any kernel of this step
-  if (S->ins_n > 0) {
-    GT_CUDA(cudaMemcpyAsync(S->ins_d, S->ins_h, (size_t)S->ins_n * t->d_in * sizeof(float),
-                            cudaMemcpyHostToDevice, s));
-    gt_status st = gt_insert(t, S->ins_d, S->ins_n, s);
-    if (st != GT_OK) return st;
-    S->st.inserted += S->ins_n;
-    S->ins_n = 0;
-  }
+  gt_status st_ins = apply_inserts(S);
+  if (st_ins != GT_OK) return st_ins;
   const int p = (int)(S->step_no & 1), np = 1 - p;
   const int cut = S->cut;
   // next-parity list counts, results, rechecks and flags start at zero
@@ -466,36 +621,15 @@ gt_status gt_server_step(gt_server *S, int64_t *in_flight) {
       fresh = &g;
       break;
     }
-  if (fresh && S->ring_size > 0) {
-    b = std::min<int64_t>(S->ring_size, S->max_group);
-    if (S->est_pairs_per_query > 0) {
-      // a group's level-(c-1) entries at most double per level below, so
-      // admit what fits a list's entries / 2^(c-1) with a 25% margin
-      const double lim = (double)(list_entries(S) >> (S->cut - 1));
-      const int64_t fit = (int64_t)(lim / (1.25 * S->est_pairs_per_query));
-      b = std::max<int64_t>(1, std::min(b, fit));
-    }
-  }
+  // (the drain schedule's lists below the cutover are the warps' own)
+  if (fresh) b = admit_count(S, S->drain ? list_entries(S) : list_entries(S) >> (S->cut - 1));
   int64_t fresh_s0 = 0;
   if (b > 0) {
     const int ring = (int)(fresh - S->groups.data());
     fresh_s0 = (int64_t)ring * S->group_stride;
-    const int d = t->d_in;
-    // the oldest b queued queries: one or two contiguous pieces of the ring
-    const int64_t k0 = S->ring_head, n1 = std::min(b, S->ring_cap - k0), n2 = b - n1;
-    GT_CUDA(cudaMemcpyAsync(S->stage, S->ring_q + k0 * d, (size_t)n1 * d * sizeof(float),
-                            cudaMemcpyHostToDevice, s));
-    GT_CUDA(cudaMemcpyAsync(S->stage + (size_t)b * d, S->ring_rho + k0, (size_t)n1 * sizeof(float),
-                            cudaMemcpyHostToDevice, s));
-    if (n2 > 0) {
-      GT_CUDA(cudaMemcpyAsync(S->stage + (size_t)n1 * d, S->ring_q, (size_t)n2 * d * sizeof(float),
-                              cudaMemcpyHostToDevice, s));
-      GT_CUDA(cudaMemcpyAsync(S->stage + (size_t)b * d + n1, S->ring_rho, (size_t)n2 * sizeof(float),
-                              cudaMemcpyHostToDevice, s));
-    }
     // queries into their slots; the GEMM then names them by slot number
-    gt_tree vq = view_of(S, t->N, fresh_s0);
-    launch_prep_queries(&vq, S->stage, S->stage + (size_t)b * d, b, s);
+    gt_status st_q = stage_queries(S, b, fresh_s0);
+    if (st_q != GT_OK) return st_q;
     gt_tree v = view_of(S, t->N, 0);
     gt_status st = launch_dense(&v, cut, S->sub ? 3 : 0, fresh_s0, b, S->gemm_out,
                                 S->counters + 2 * (cut - 1) + np, s);
@@ -510,10 +644,8 @@ gt_status gt_server_step(gt_server *S, int64_t *in_flight) {
                           cudaMemcpyDeviceToHost, s));
   GT_CUDA(cudaStreamSynchronize(s));
   const uint32_t *hc = S->hcounters;
-  if (hc[64 + kFlagTimeout]) return set_error(GT_ETIMEOUT, "a bounded device wait expired");
-  if (hc[64 + kFlagDomain])
-    return set_error(GT_EDOMAIN, t->split_sign ? "a query has a non-finite entry"
-                                               : "a query has a negative or non-finite entry");
+  gt_status st_f = step_flags(S, hc);
+  if (st_f != GT_OK) return st_f;
   if (hc[64 + kFlagStray]) {
     std::string lv;
     for (auto &g : S->groups)
@@ -655,7 +787,9 @@ gt_status gt_server_get_stats(const gt_server *S, gt_server_stats *out) {
   out->pending = S->ring_size;
   out->cutover = S->cut;
   out->max_group = S->max_group;
-  out->schedule = S->drain ? GT_SCHEDULE_DRAIN : GT_SCHEDULE_LEVELS;
+  out->schedule = S->immediate ? GT_SCHEDULE_IMMEDIATE
+                 : S->drain    ? GT_SCHEDULE_DRAIN
+                               : GT_SCHEDULE_LEVELS;
   return GT_OK;
 }
 

@@ -68,7 +68,7 @@ class AutotuneResult(ctypes.Structure):
                 ("subtract", _c_i32)]
 
 
-SCHEDULES = {"auto": 0, "levels": 1, "drain": 2}
+SCHEDULES = {"auto": 0, "levels": 1, "drain": 2, "immediate": 3}
 
 
 class ServerOpts(ctypes.Structure):

@@ -114,16 +114,18 @@ def test_prefix_served_equals_alone(gt, stream_ds):
         alone.close()
 
 
+@pytest.mark.parametrize("schedule", ["drain", "immediate"])
 @pytest.mark.parametrize("dtype", ["bf16", "fp8"])
-def test_drain_server_exact_with_inserts(gt, stream_ds, dtype):
-    # tests in flight code 32: each step drains the group admitted the step
-    # before (every level below the cutover and its items in one launch)
-    # while it admits the next
+def test_drain_server_exact_with_inserts(gt, stream_ds, dtype, schedule):
+    # tests in flight code 32: one launch takes a group through every level
+    # below the cutover and its items, either the step after its admission
+    # (drain: while the step admits the next group) or in the step that
+    # admits it (immediate)
     ds = stream_ds
     n0 = 40_000
     t = gt.Tree(ds.F[:n0], capacity=ds.F.shape[0])
-    done, st = _serve(gt, t, ds, n0, dtype, max_group=64, insert_every=3, schedule="drain")
-    assert st["schedule"] == 2
+    done, st = _serve(gt, t, ds, n0, dtype, max_group=64, insert_every=3, schedule=schedule)
+    assert st["schedule"] == {"drain": 2, "immediate": 3}[schedule]
     assert st["completed"] == ds.Q.shape[0] and st["inserted"] == ds.F.shape[0] - n0
     by_snap = {}
     for tag, (ids, snap) in done.items():
@@ -137,7 +139,7 @@ def test_drain_server_exact_with_inserts(gt, stream_ds, dtype):
             assert np.array_equal(done[tag][0], ref.neighbours(i)), f"query {tag} (N={snap})"
     # the same tests as the level-by-level server (one group at a time)
     srv_counts = {}
-    for code in ("levels", "drain"):
+    for code in ("levels", schedule):
         srv = gt.Server(t, dtype=dtype, max_group=4096, schedule=code)
         srv.submit(ds.Q, ds.rho, np.arange(ds.Q.shape[0]))
         got = {}
@@ -152,8 +154,11 @@ def test_drain_server_exact_with_inserts(gt, stream_ds, dtype):
         ref = oracle.brute_force(ds.F, ds.Q, ds.rho)
         for tag in range(ds.Q.shape[0]):
             assert np.array_equal(got[tag], ref.neighbours(tag))
-    assert srv_counts["drain"]["gathered_tests"] == srv_counts["levels"]["gathered_tests"]
-    assert srv_counts["drain"]["steps"] < srv_counts["levels"]["steps"]
+    assert srv_counts[schedule]["gathered_tests"] == srv_counts["levels"]["gathered_tests"]
+    assert srv_counts[schedule]["steps"] < srv_counts["levels"]["steps"]
+    if schedule == "immediate":
+        # the whole queue fits one group: answered by the first step
+        assert srv_counts[schedule]["steps"] == 1
     t.close()
 
 
@@ -201,6 +206,8 @@ def test_insert_into_a_tail_pool_gives_no_lower_bound(gt, schedule):
     # bound covers the new item too, so it must not travel as the pool's
     # lower bound: item 3998 (scoring below rho) would be accepted without
     # its row as the pool's bound minus nothing (no right item in the view).
+    # (The immediate schedule answers a group within the step that admits
+    # it, before any later insert.)
     rng = np.random.default_rng(29)
     d, n0 = 64, 3999
     F = np.exp(3 * rng.standard_normal((n0 + 1, d)))
@@ -236,7 +243,7 @@ def test_served_equals_alone(gt, stream_ds):
     n0 = 40_000
     t = gt.Tree(ds.F[:n0], capacity=ds.F.shape[0])
     done, st = _serve(gt, t, ds, n0, "bf16", max_group=128, insert_every=5)
-    assert st["schedule"] == 2                               # the automatic choice here
+    assert st["schedule"] == 3                               # the automatic choice here
     t.close()
     rng = np.random.default_rng(9)
     for tag in rng.choice(ds.Q.shape[0], 12, replace=False):
@@ -258,13 +265,17 @@ def test_server_without_inserts_matches_batch_query(gt, stream_ds):
     t.close()
 
 
-def test_server_admission_backs_off_on_overflow(gt, stream_ds):
+@pytest.mark.parametrize("schedule", ["levels", "immediate"])
+def test_server_admission_backs_off_on_overflow(gt, stream_ds, schedule):
     ds = stream_ds
     t = gt.Tree(ds.F)
     # a frontier budget far below one full group's survivors: groups are cut
-    # until they fit, and every answer is still exact
-    srv = gt.Server(t, dtype="bf16", max_group=512, scratch_bytes=1 << 21, schedule="levels")
-    srv.submit(ds.Q, ds.rho, np.arange(ds.Q.shape[0]))
+    # until they fit, and every answer is still exact (the immediate schedule
+    # drops an overflowed group's answers and answers it again, smaller; its
+    # GEMM list may fill the whole budget, so a lower rho makes it overflow)
+    rho = ds.rho if schedule == "levels" else np.full(ds.Q.shape[0], 0.65, np.float32)
+    srv = gt.Server(t, dtype="bf16", max_group=512, scratch_bytes=1 << 21, schedule=schedule)
+    srv.submit(ds.Q, rho, np.arange(ds.Q.shape[0]))
     done = {}
     for _ in range(5000):
         srv.step()
@@ -275,7 +286,7 @@ def test_server_admission_backs_off_on_overflow(gt, stream_ds):
     st = srv.stats()
     srv.close()
     assert st["retries"] >= 1 and st["max_group"] < 512
-    ref = t.query(ds.Q, ds.rho, dtype="bf16")
+    ref = t.query(ds.Q, rho, dtype="bf16")
     for tag in range(ds.Q.shape[0]):
         assert np.array_equal(done[tag], ref.neighbours(tag))
     t.close()
