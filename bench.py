@@ -232,7 +232,7 @@ def _dist():
 
 
 def serve_run(gt, tree, Q, rhos, rate, n_req, dtype, inserts=None, insert_frac=0.01, seed=0,
-              schedule="auto", rho_per_query=None):
+              schedule="auto", rho_per_query=None, cutover=-1):
     """Poisson request stream through the continuous-batching server.
 
     Returns achieved queries/s (completed / span from first arrival to last
@@ -248,7 +248,7 @@ def serve_run(gt, tree, Q, rhos, rate, n_req, dtype, inserts=None, insert_frac=0
     rho = (rho_per_query[qi] if rho_per_query is not None
            else rhos[rng.integers(0, len(rhos), n_req)]).astype(np.float32)
     is_ins = rng.random(n_req) < insert_frac if inserts is not None else np.zeros(n_req, bool)
-    srv = gt.Server(tree, dtype=dtype, queue_capacity=n_req, schedule=schedule)
+    srv = gt.Server(tree, dtype=dtype, queue_capacity=n_req, schedule=schedule, cutover=cutover)
     lat = np.full(n_req, np.nan)
     sub = 0
     n_done = 0

@@ -438,7 +438,10 @@ typedef struct gt_server_opts {
  *                          answered at the end of the first step that starts
  *                          after it arrives, and no group stays in flight
  *                          between steps.  A group whose lists overflow is
- *                          answered again, smaller, by a later step.
+ *                          answered again, smaller, by a later step.  A group
+ *                          of at most 64 queries has its GEMM one or two
+ *                          levels above the server's cutover (at most level
+ *                          5), where the GEMM reads fewer pool rows.
  *   GT_SCHEDULE_AUTO       GT_SCHEDULE_IMMEDIATE where it applies, else
  *                          GT_SCHEDULE_LEVELS.
  * DRAIN and IMMEDIATE need the subtraction path (sum pools, cutover 2 to 5,

@@ -296,6 +296,10 @@ gt_status step_flags(gt_server *S, const uint32_t *hc) {
   return GT_OK;
 }
 
+// Groups of at most this many queries skip the grouping by query before
+// k_drain (GT_SCHEDULE_IMMEDIATE).
+constexpr int64_t kUngroupedMax = 64;
+
 // GT_SCHEDULE_IMMEDIATE: one step admits a group from the queue's head and
 // answers it: the dense GEMM at the cutover, its survivors grouped by query,
 // one persistent launch for every level below and the items (k_drain), the
@@ -311,9 +315,24 @@ gt_status step_immediate(gt_server *S, int64_t *in_flight) {
   gt_status st = apply_inserts(S);
   if (st != GT_OK) return st;
   const int p = (int)(S->step_no & 1), np = 1 - p;
-  const int cut = S->cut;
   const int64_t room = list_entries(S);
   const int64_t b = admit_count(S, room);
+  // The dense level: the server's for large groups; for small ones (not
+  // grouped by query) one or two levels higher, up to k_drain's limit.  The
+  // GEMM's floor is a read of every pool row at its level, which halves per
+  // level up, while the levels gathered below it add work in proportion to
+  // the group (measured at N = 1M, d = 1000: groups of about 10 queries are
+  // answered 13% sooner with the GEMM at level 5 than at level 3, groups of
+  // about 200 fastest at level 3).
+  int cut = S->cut;
+  if (b <= kUngroupedMax) {
+    const int up = std::min<int>(std::min(S->cut + (b <= 32 ? 2 : 1), 5), t->L);
+    for (int c = up; c > S->cut; --c)
+      if (drain_available(t, S->fmt, c)) {
+        cut = c;
+        break;
+      }
+  }
   int64_t launches = 0;
   if (b > 0) {
     k_step_reset<<<1, 64, 0, s>>>(S->counters, np, cut);
@@ -325,9 +344,17 @@ gt_status step_immediate(gt_server *S, int64_t *in_flight) {
     uint32_t *gemm_count = S->counters + 2 * (cut - 1) + np;
     st = launch_dense(&v, cut, 3, s0, b, S->gemm_out, gemm_count, s);
     if (st != GT_OK) return st;
-    launch_bucket(&v, true, S->gemm_out, S->lists[cut - 1][np], gemm_count, (uint32_t)room, s0, b, s);
-    launch_drain(&v, S->fmt, cut, reinterpret_cast<const SibPair *>(S->lists[cut - 1][np]), gemm_count,
-                 s, S->counters + kDrainCounts, S->counters + kDrainCounts + 8);
+    // a small group's GEMM list goes to k_drain as it is (its warps then
+    // take one or a few entries each, one query apiece); a large one is first
+    // grouped by query, so that a warp's entries share their query
+    const SibPair *queue = reinterpret_cast<const SibPair *>(S->gemm_out);
+    if (b > kUngroupedMax) {
+      launch_bucket(&v, true, S->gemm_out, S->lists[cut - 1][np], gemm_count, (uint32_t)room, s0, b, s);
+      queue = reinterpret_cast<const SibPair *>(S->lists[cut - 1][np]);
+      launches += 4;
+    }
+    launch_drain(&v, S->fmt, cut, queue, gemm_count, s, S->counters + kDrainCounts,
+                 S->counters + kDrainCounts + 8);
     launch_recheck(&v, 0, s);
     GT_CUDA(cudaMemsetAsync(S->cnt + s0, 0, (size_t)(b + 1) * sizeof(int64_t), s));
     launch_csr_into(&v, S->res, (uint32_t)S->res_cap, S->counters + kMaxLevels, s0, b, S->cnt, S->off,
@@ -339,7 +366,7 @@ gt_status step_immediate(gt_server *S, int64_t *in_flight) {
     GT_CUDA(cudaGetLastError());
     GT_CUDA(cudaMemcpyAsync(S->hcounters, S->counters, 128 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     GT_CUDA(cudaStreamSynchronize(s));
-    launches += 16;  // prep, thresholds, GEMM, 4 grouping, drain, recheck, 6 CSR, reset
+    launches += 12;  // reset, prep, thresholds, GEMM, drain, recheck, 6 CSR
     const uint32_t *hc = S->hcounters;
     st = step_flags(S, hc);
     if (st != GT_OK) return st;
@@ -355,7 +382,7 @@ gt_status step_immediate(gt_server *S, int64_t *in_flight) {
       if (b == 1)
         return set_error(GT_EOVERFLOW, "one query's frontier or neighbours exceed the server's budget");
       S->max_group = std::max<int64_t>(1, b / 2);
-      S->est_pairs_per_query = std::max(S->est_pairs_per_query, per_q);
+      if (cut == S->cut) S->est_pairs_per_query = std::max(S->est_pairs_per_query, per_q);
       ++S->st.retries;
     } else {
       const int64_t first = S->hoff[0], n_ids = S->hoff[b] - first;
@@ -375,7 +402,8 @@ gt_status step_immediate(gt_server *S, int64_t *in_flight) {
       }
       S->ring_head = (S->ring_head + b) % S->ring_cap;
       S->ring_size -= b;
-      S->est_pairs_per_query = std::max(S->est_pairs_per_query * 0.9, per_q);
+      // (the admission estimate is kept in the server's own level's terms)
+      if (cut == S->cut) S->est_pairs_per_query = std::max(S->est_pairs_per_query * 0.9, per_q);
       S->st.admitted += b;
       S->st.completed += b;
       S->st.rechecks += hc[kMaxLevels + 1];

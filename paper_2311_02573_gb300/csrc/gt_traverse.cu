@@ -1554,13 +1554,18 @@ __global__ void __launch_bounds__(32 * kRingWarps, 1)
     }
   };
 
+  // entries per claim: 32, or fewer when the queue is short (a small served
+  // group), so that its subtrees spread over as many warps as the grid has
+  // instead of queuing behind one another in a few warps
+  const uint32_t n_warps = gridDim.x * kRingWarps;
+  const uint32_t claim = max(1u, min(32u, (n_root + n_warps - 1u) / n_warps));
   while (ok) {
-    // claim the next 32 entries of the queue
+    // claim the next entries of the queue
     uint32_t base = 0;
-    if (lane == 0) base = atomicAdd(g.head, 32u);
+    if (lane == 0) base = atomicAdd(g.head, claim);
     base = __shfl_sync(FULL, base, 0);
     if (base >= n_root) break;
-    const uint32_t cnt = min(32u, n_root - base);
+    const uint32_t cnt = min(claim, n_root - base);
     // a queue entry naming a query or a row outside its buffers can only
     // come from a corrupted list: flagged, and its subtree left out
     bool bad = false;
