@@ -301,7 +301,7 @@ void gemm_bound(int h, double *cu, double *cl);
 // the ring-fed gather's slots do not fit rows of this format and width.
 bool launch_prefix(gt_tree *t, int fmt, int h, const SibPair *in, const uint32_t *in_count,
                    SibPair *out, uint32_t *out_count, cudaStream_t s);
-void launch_recheck(gt_tree *t, int64_t q0, cudaStream_t s);
+void launch_recheck(gt_tree *t, int64_t q0, cudaStream_t s, int max_blocks = 0);
 // The level kernels' test of n given (query, pool) pairs at level h: score,
 // upper and lower bound per pair into out (gt_pair_bounds).
 void launch_pair_bounds(gt_tree *t, int fmt, int h, const int32_t *pairs, int64_t n, int64_t n_queries,

@@ -355,7 +355,7 @@ gt_status step_immediate(gt_server *S, int64_t *in_flight) {
     }
     launch_drain(&v, S->fmt, cut, queue, gemm_count, s, S->counters + kDrainCounts,
                  S->counters + kDrainCounts + 8);
-    launch_recheck(&v, 0, s);
+    launch_recheck(&v, 0, s, b <= kUngroupedMax ? t->sm_count : 0);
     GT_CUDA(cudaMemsetAsync(S->cnt + s0, 0, (size_t)(b + 1) * sizeof(int64_t), s));
     launch_csr_into(&v, S->res, (uint32_t)S->res_cap, S->counters + kMaxLevels, s0, b, S->cnt, S->off,
                     S->ids, S->counters + kCsrListSlot, s);
@@ -366,7 +366,9 @@ gt_status step_immediate(gt_server *S, int64_t *in_flight) {
     GT_CUDA(cudaGetLastError());
     GT_CUDA(cudaMemcpyAsync(S->hcounters, S->counters, 128 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     GT_CUDA(cudaStreamSynchronize(s));
-    launches += 12;  // reset, prep, thresholds, GEMM, drain, recheck, 6 CSR
+    // reset, prep, thresholds, GEMM, drain, recheck, and the CSR's (one block
+    // and its long-segment sort for a small group)
+    launches += 6 + (b <= 64 ? 2 : 6);
     const uint32_t *hc = S->hcounters;
     st = step_flags(S, hc);
     if (st != GT_OK) return st;

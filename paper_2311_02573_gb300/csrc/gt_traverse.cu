@@ -1969,24 +1969,14 @@ __device__ void bitonic(int32_t *a, int64_t n) {
   }
 }
 
-// Segments of lo < n <= 32 KPL ids: one warp, KPL ids per lane (id index
-// i = 32 k + lane), a bitonic network whose partners i ^ stride sit in
-// another lane (stride < 32, a shuffle) or another register of the same lane.
-// Longer segments are appended to `list` (when given) for k_csr_sort.
+// Ascending sort of one segment of n <= 32 KPL ids, ids[s .. s + n), by one
+// warp: KPL ids per lane (id index i = 32 k + lane), a bitonic network whose
+// partners i ^ stride sit in another lane (stride < 32, a shuffle) or another
+// register of the same lane.
 template <int KPL>
-__global__ void __launch_bounds__(256) k_csr_sort_warp(const int64_t *off, int32_t *ids, int64_t B,
-                                                       int64_t lo, int64_t *list,
-                                                       uint32_t *list_n) {
+__device__ __forceinline__ void warp_sort_ids(int32_t *ids, int64_t s, int64_t n) {
   constexpr int CAP = 32 * KPL;
   const int lane = threadIdx.x & 31;
-  const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (q >= B) return;
-  const int64_t s = off[q], n = off[q + 1] - s;
-  if (n > CAP) {
-    if (list && lane == 0) list[atomicAdd(list_n, 1u)] = q;
-    return;
-  }
-  if (n <= lo || n <= 1) return;
   int32_t v[KPL];
 #pragma unroll
   for (int k = 0; k < KPL; ++k) {
@@ -2021,6 +2011,86 @@ __global__ void __launch_bounds__(256) k_csr_sort_warp(const int64_t *off, int32
   for (int k = 0; k < KPL; ++k) {
     const int i = 32 * k + lane;
     if (i < n) ids[s + i] = v[k];
+  }
+}
+
+// Segments of lo < n <= 32 KPL ids, one warp each.  Longer segments are
+// appended to `list` (when given) for k_csr_sort.
+template <int KPL>
+__global__ void __launch_bounds__(256) k_csr_sort_warp(const int64_t *off, int32_t *ids, int64_t B,
+                                                       int64_t lo, int64_t *list,
+                                                       uint32_t *list_n) {
+  constexpr int CAP = 32 * KPL;
+  const int lane = threadIdx.x & 31;
+  const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (q >= B) return;
+  const int64_t s = off[q], n = off[q + 1] - s;
+  if (n > CAP) {
+    if (list && lane == 0) list[atomicAdd(list_n, 1u)] = q;
+    return;
+  }
+  if (n <= lo || n <= 1) return;
+  warp_sort_ids<KPL>(ids, s, n);
+}
+
+// The CSR of a few queries (B <= kCsrSmallMax) in one block: counts per query
+// in shared memory, their scan, the fill (ids through the tree permutation)
+// and the sort of each query's ids by one warp; segments longer than a warp
+// sorts are listed for k_csr_sort.  One launch instead of the six of the
+// general passes: a served group's step is bound by such fixed costs.
+constexpr int kCsrSmallMax = 64;
+__global__ void __launch_bounds__(1024) k_csr_small(const Pair *res, uint32_t n_cap,
+                                                    const uint32_t *n_dev, uint32_t q_lo,
+                                                    uint32_t B, int64_t *off_r,
+                                                    const int32_t *perm, int32_t *ids,
+                                                    int64_t *list, uint32_t *list_n, int *flags) {
+  __shared__ uint32_t cnt[kCsrSmallMax + 1], cur[kCsrSmallMax + 1];
+  __shared__ int64_t start[kCsrSmallMax + 1];
+  const uint32_t tid = threadIdx.x;
+  if (tid <= B) {
+    cnt[tid] = 0u;
+    cur[tid] = 0u;
+  }
+  if (tid == 0) *list_n = 0u;
+  __syncthreads();
+  const uint32_t n = csr_n(n_cap, n_dev);
+  for (uint32_t i = tid; i < n; i += blockDim.x) {
+    const Pair p = res[i];
+    if (p.q < q_lo || p.q - q_lo >= B) {  // not a query of this range: flagged, left out
+      if (atomicExch(&flags[kFlagStray], 1) == 0) {
+        flags[kFlagStray + 1] = (int)p.q;
+        flags[kFlagStray + 2] = (int)p.j;
+      }
+      continue;
+    }
+    atomicAdd(&cnt[p.q - q_lo], 1u);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int64_t run = 0;
+    for (uint32_t q = 0; q < B; ++q) {
+      start[q] = run;
+      run += cnt[q];
+    }
+    start[B] = run;
+  }
+  __syncthreads();
+  if (tid <= B) off_r[tid] = start[tid];
+  for (uint32_t i = tid; i < n; i += blockDim.x) {
+    const Pair p = res[i];
+    if (p.q < q_lo || p.q - q_lo >= B) continue;
+    const uint32_t q = p.q - q_lo;
+    ids[start[q] + atomicAdd(&cur[q], 1u)] = perm[p.j];
+  }
+  __syncthreads();  // the block's writes of ids before its warps read them back
+  const uint32_t warp = tid >> 5, lane = tid & 31u;
+  for (uint32_t q = warp; q < B; q += blockDim.x >> 5) {
+    const int64_t m = cnt[q];
+    if (m > 512) {
+      if (lane == 0) list[atomicAdd(list_n, 1u)] = q;
+    } else if (m > 1) {
+      warp_sort_ids<16>(ids, start[q], m);
+    }
   }
 }
 
@@ -2744,10 +2814,13 @@ bool items_sub_available(gt_tree *t, int fmt) {
   return ring_depth((int)((t->d * entry_bytes(fmt) + 15) / 16), &slot) > 0;
 }
 
-void launch_recheck(gt_tree *t, int64_t /*q0*/, cudaStream_t s) {
+void launch_recheck(gt_tree *t, int64_t /*q0*/, cudaStream_t s, int max_blocks) {
   Workspace &w = t->ws;
   static int per_sm = 0;
-  const int grid = grid_for((const void *)k_recheck, 256, t->sm_count, per_sm);
+  // (max_blocks: a smaller grid for a step that rechecks few items, where
+  // scheduling a full grid of blocks that find no work costs more than it)
+  int grid = grid_for((const void *)k_recheck, 256, t->sm_count, per_sm);
+  if (max_blocks > 0) grid = std::min(grid, max_blocks);
   k_recheck<<<grid, 256, 0, s>>>(w.rchk, w.counters + kMaxLevels + 1, (uint32_t)w.rchk_cap,
                                  t->rows32, t->stride, (int)((t->d + 3) / 4),
                                  t->split_sign ? t->d_in : 0, w.qf32, w.rho, w.res,
@@ -2770,6 +2843,14 @@ void launch_csr_into(gt_tree *t, const Pair *res, uint32_t n, const uint32_t *n_
   // arrays by query, the scan and the sorts see the range only
   int64_t *cnt_r = cnt + q_lo, *off_r = off + q_lo;
   const uint32_t q_hi = (uint32_t)(q_lo + B);
+  if (B >= 1 && B <= kCsrSmallMax) {
+    // one block for the CSR of a few queries; its long segments (listed in
+    // cnt_r, then unused) sorted after it
+    k_csr_small<<<1, 1024, 0, s>>>(res, n, n_dev, (uint32_t)q_lo, (uint32_t)B, off_r, t->perm, ids,
+                                   cnt_r, list_n, t->flags);
+    k_csr_sort<<<(unsigned)B, 256, 0, s>>>(off_r, ids, cnt_r, list_n);
+    return;
+  }
   if (any) k_csr_count<<<blocks, 256, 0, s>>>(res, n, n_dev, (uint32_t)q_lo, q_hi, cnt, t->flags);
   k_scan<<<1, 1024, 0, s>>>(cnt_r, B, off_r);
   cudaMemsetAsync(cnt_r, 0, (size_t)(B + 1) * sizeof(int64_t), s);
