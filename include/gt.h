@@ -471,7 +471,10 @@ gt_status gt_server_create(gt_tree *t, const gt_server_opts *opts, gt_server **o
 /* Queue n queries (host Q n x d, rho n, caller tags n); copied on return. */
 gt_status gt_server_submit(gt_server *s, const float *Q, const float *rho, const int64_t *tags,
                            int64_t n);
-/* Queue n rows (host, n x d) for insertion at the start of the next step. */
+/* Queue n rows (host, n x d) for insertion at the start of the next step.
+ * The rows are checked here (GT_EDOMAIN for a negative or non-finite entry,
+ * or a non-finite one for a GT_POOL_MAXMIN tree; nothing of the call is
+ * queued then), so that the step applies them without waiting on the device. */
 gt_status gt_server_insert(gt_server *s, const float *f, int64_t n);
 /* One engine iteration (synchronous).  *in_flight: queries on the device. */
 gt_status gt_server_step(gt_server *s, int64_t *in_flight);

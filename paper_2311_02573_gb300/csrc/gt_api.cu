@@ -281,6 +281,29 @@ gt_status scan_context(int dev, int64_t N, int32_t d, gt_tree **out) {
 
 using namespace gt;
 
+namespace gt {
+// Append n_new device rows that the caller has already checked (finite, and
+// non-negative unless the tree stores split signed rows): the items' rows,
+// then every pool above them, enqueued on s with no wait for the device
+// (storage grows first, synchronously, when the capacity is reached).
+gt_status insert_checked_async(gt_tree *t, const float *F_dev, int64_t n_new, cudaStream_t s) {
+  if (n_new <= 0) return GT_OK;
+  const int64_t N1 = t->N + n_new;
+  if (N1 >= ((int64_t)1 << 31)) return set_error(GT_EINVAL, "tree would exceed 2^31 items");
+  if (N1 > t->cap) {
+    gt_status st = grow(t, std::max<int64_t>(N1, 2 * t->cap));
+    if (st != GT_OK) return st;
+  }
+  gt_status st = tree_build_level0(t, F_dev, t->N, n_new, nullptr, s);
+  if (st != GT_OK) return st;
+  const int64_t first = t->N;
+  t->N = N1;
+  t->L = top_level(N1);
+  return t->layout == GT_LAYOUT_PREFIX ? prefix_build(t, first, n_new, s)
+                                       : tree_build_levels(t, first, n_new, s);
+}
+}  // namespace gt
+
 extern "C" {
 
 const char *gt_last_error(void) { return g_err.c_str(); }

@@ -227,6 +227,9 @@ float tree_norm_dev(gt_tree *t);
 // block totals of the blocks covering items [first, first + n)
 gt_status prefix_alloc(gt_tree *t, int64_t cap);
 gt_status prefix_build(gt_tree *t, int64_t first, int64_t n, cudaStream_t s);
+// gt_insert's work without its checks and waits (gt_api.cu): for rows the
+// caller has validated on the host; enqueued on s
+gt_status insert_checked_async(gt_tree *t, const float *F_dev, int64_t n_new, cudaStream_t s);
 
 // query-side kernels (gt_traverse.cu)
 gt_status ws_reserve_queries(gt_tree *t, int64_t B);

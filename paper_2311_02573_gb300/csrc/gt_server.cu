@@ -23,6 +23,7 @@
 // that snapshot (later inserts only raise pool sums, so the bounds stay
 // valid), so a query's answer is the same alone and in the mix.
 #include <algorithm>
+#include <cmath>
 #include <chrono>
 #include <cstring>
 #include <deque>
@@ -242,12 +243,15 @@ double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
-// Queued inserts, in one batch, before any kernel of the step.
+// Queued inserts, in one batch, before any kernel of the step (the rows were
+// checked by gt_server_insert; nothing here waits for the device).  The step
+// synchronizes before it returns, so the pinned staging rows are not reused
+// while their copy is in flight.
 gt_status apply_inserts(gt_server *S) {
   if (S->ins_n == 0) return GT_OK;
   GT_CUDA(cudaMemcpyAsync(S->ins_d, S->ins_h, (size_t)S->ins_n * S->t->d_in * sizeof(float),
                           cudaMemcpyHostToDevice, S->s));
-  gt_status st = gt_insert(S->t, S->ins_d, S->ins_n, S->s);
+  gt_status st = insert_checked_async(S->t, S->ins_d, S->ins_n, S->s);
   if (st != GT_OK) return st;
   S->st.inserted += S->ins_n;
   S->ins_n = 0;
@@ -312,6 +316,7 @@ gt_status step_immediate(gt_server *S, int64_t *in_flight) {
   gt_tree *t = S->t;
   cudaStream_t s = S->s;
   const double t0 = now_s();
+  const bool inserting = S->ins_n > 0;
   gt_status st = apply_inserts(S);
   if (st != GT_OK) return st;
   const int p = (int)(S->step_no & 1), np = 1 - p;
@@ -416,6 +421,7 @@ gt_status step_immediate(gt_server *S, int64_t *in_flight) {
       S->st.gathered_tests += hc[kDrainCounts + 8];
     }
   }
+  if (b == 0 && inserting) GT_CUDA(cudaStreamSynchronize(s));  // the inserts' copy and kernels
   S->step_no += 1;
   S->st.steps += 1;
   S->st.launches += launches;
@@ -543,6 +549,15 @@ gt_status gt_server_submit(gt_server *S, const float *Q, const float *rho, const
 gt_status gt_server_insert(gt_server *S, const float *f, int64_t n) {
   if (!S || (n > 0 && !f)) return set_error(GT_EINVAL, "null argument");
   const int d = S->t->d_in;
+  // checked here, on the host, so that a step applies queued rows without
+  // waiting for the device to check them (the rule gt_insert applies)
+  const bool signed_rows = S->t->split_sign;
+  for (int64_t i = 0; i < n * (int64_t)d; ++i) {
+    const float x = f[i];
+    if (!std::isfinite(x) || (!signed_rows && x < 0.f))
+      return set_error(GT_EDOMAIN, signed_rows ? "inserted row has a non-finite entry"
+                                               : "inserted row has a negative or non-finite entry");
+  }
   if (S->ins_n + n > S->ins_cap) {
     int64_t cap = S->ins_cap;
     while (cap < S->ins_n + n) cap *= 2;

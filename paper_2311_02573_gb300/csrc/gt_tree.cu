@@ -204,6 +204,81 @@ __global__ void __launch_bounds__(512) k_levels_small(RowsOut o, LevelRange lr, 
   }
 }
 
+// A short append (at most kChainRows rows to recompute at each of levels
+// h0..h1): one block keeps each level's new FP32 rows in shared memory for the
+// level above, and loads at the start, all at once, the rows it reads from
+// memory: level h0-1's rows of the range and, for every level, the one
+// existing row that can be a child of a new row (the left sibling of the
+// range's first row, when that row is a right child).  A level is then a sum
+// in shared memory and the rows' writes: the same sums, in the same order,
+// as k_levels_small, without a dependent read from memory per level.
+constexpr int kChainRows = 4;
+
+template <int KV4>
+__global__ void __launch_bounds__(256) k_levels_chain(RowsOut o, LevelRange lr, int h0, int h1) {
+  extern __shared__ float4 chain_sm[];
+  const int nv4 = (int)(o.stride / 4);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  float4 *prev = chain_sm;                       // 2 kChainRows rows
+  float4 *cur = prev + 2 * kChainRows * nv4;     // kChainRows rows
+  float4 *sib = cur + kChainRows * nv4;          // one row per level h0..h1
+  const int n_first = (int)(lr.hi[h0 - 1] - lr.lo[h0 - 1]);
+  const int n_lv = h1 - h0 + 1;
+  for (int task = warp; task < n_first + n_lv; task += nw) {
+    int64_t row;
+    float4 *dst;
+    if (task < n_first) {
+      row = lr.base[h0 - 1] + lr.lo[h0 - 1] + task;
+      dst = prev + (int64_t)task * nv4;
+    } else {
+      const int h = h0 + (task - n_first);
+      const int64_t lo1 = lr.lo[h - 1];
+      if ((lo1 & 1) == 0) continue;  // the first new row at h-1 is a left child
+      row = lr.base[h - 1] + lo1 - 1;
+      dst = sib + (int64_t)(h - h0) * nv4;
+    }
+    const float4 *src = reinterpret_cast<const float4 *>(o.r32 + row * o.stride);
+    for (int i = lane; i < nv4; i += 32) dst[i] = src[i];
+  }
+  __syncthreads();
+  for (int h = h0; h <= h1; ++h) {
+    const int64_t lo1 = lr.lo[h - 1], rows1 = lr.rows[h - 1];
+    const int n_cur = (int)(lr.hi[h] - lr.lo[h]);
+    if (warp < n_cur) {
+      const int64_t j = lr.lo[h] + warp;
+      // child 2j always exists (j < rows at h); it is a new row of level h-1,
+      // or (below the range) the loaded sibling; child 2j+1 may be missing
+      const float4 *a = 2 * j >= lo1 ? prev + (2 * j - lo1) * nv4 : sib + (int64_t)(h - h0) * nv4;
+      const bool has_b = 2 * j + 1 < rows1;
+      const float4 *b = prev + (2 * j + 1 - lo1) * nv4;
+      float4 v[KV4];
+#pragma unroll
+      for (int k = 0; k < KV4; ++k) {
+        const int i = lane + 32 * k;
+        if (i < nv4) {
+          float4 x = a[i];
+          if (has_b) {
+            const float4 y = b[i];
+            if (o.max_pool) {
+              x.x = fmaxf(x.x, y.x); x.y = fmaxf(x.y, y.y); x.z = fmaxf(x.z, y.z); x.w = fmaxf(x.w, y.w);
+            } else {
+              x.x += y.x; x.y += y.y; x.z += y.z; x.w += y.w;
+            }
+          }
+          v[k] = x;
+          cur[(int64_t)warp * nv4 + i] = x;
+        } else {
+          v[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+      }
+      write_row<KV4>(o, lr.base[h] + j, v, nv4);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < n_cur * nv4; t += blockDim.x) prev[t] = cur[t];
+    __syncthreads();
+  }
+}
+
 RowsOut rows_out(gt_tree *t) {
   RowsOut o;
   const bool pre = t->layout == GT_LAYOUT_PREFIX;  // rows16 holds pools there, not items
@@ -375,9 +450,32 @@ gt_status tree_build_levels(gt_tree *t, int64_t first, int64_t n, cudaStream_t s
                                                                lr.base[h], lr.lo[h], lr.hi[h]));
     GT_CUDA(cudaGetLastError());
   }
-  // the remaining small levels: one block walks them in order
+  // the remaining small levels: one block walks them in order (a short
+  // append, with its rows and siblings in shared memory, when they fit)
   if (h <= t->L) {
-    GT_DISPATCH_KV4(kv, k_levels_small<KV><<<1, 512, 0, s>>>(o, lr, h, t->L));
+    const int64_t row_bytes = t->stride * (int64_t)sizeof(float);
+    const int64_t smem = (3 * kChainRows + (t->L - h + 1)) * row_bytes;
+    static int smem_max = 0;
+    if (!smem_max) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    }
+    const bool chain = lr.hi[h] - lr.lo[h] <= kChainRows && lr.hi[h - 1] - lr.lo[h - 1] <= 2 * kChainRows &&
+                       smem <= smem_max;
+    if (chain) {
+      GT_DISPATCH_KV4(kv, {
+        static bool attr = false;
+        if (!attr) {
+          GT_CUDA(cudaFuncSetAttribute(k_levels_chain<KV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       smem_max));
+          attr = true;
+        }
+        k_levels_chain<KV><<<1, 256, (size_t)smem, s>>>(o, lr, h, t->L);
+      });
+    } else {
+      GT_DISPATCH_KV4(kv, k_levels_small<KV><<<1, 512, 0, s>>>(o, lr, h, t->L));
+    }
     GT_CUDA(cudaGetLastError());
   }
   return GT_OK;

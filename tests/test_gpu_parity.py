@@ -370,6 +370,31 @@ def test_insert_equals_full_build(gt, small_ds):
     full.close()
 
 
+@pytest.mark.parametrize("pooling", ["sum", "max"])
+def test_short_appends_equal_full_build(gt, small_ds, pooling):
+    # appends of 1 to 8 rows at every parity of the tree size (the short-append
+    # path recomputes the levels from rows kept in shared memory): every level
+    # stays bitwise equal to a full build of the same rows
+    ds = small_ds
+    F = ds.F[:3100]
+    t = gt.Tree(F[:3000], capacity=3200, pooling=pooling)
+    n = 3000
+    for m in (1, 1, 2, 3, 1, 5, 8, 2, 7, 4, 1, 6, 3):
+        t.insert(F[n:n + m])
+        n += m
+        if n in (3001, 3004, 3013, 3023, 3044):
+            full = gt.Tree(F[:n], pooling=pooling)
+            for h in range(full.levels):
+                assert np.array_equal(t.read_rows(h), full.read_rows(h)), f"n {n} level {h}"
+                assert np.array_equal(t.read_rows(h, "bf16"), full.read_rows(h, "bf16"))
+                a, sa = t.read_rows(h, "fp8")
+                b, sb = full.read_rows(h, "fp8")
+                assert np.array_equal(a, b) and np.array_equal(sa, sb)
+            full.close()
+    assert n == 3044
+    t.close()
+
+
 def test_insert_crossing_power_of_two(gt):
     F, Q = _tiny(40, d=48, B=8, seed=11)
     t = gt.Tree(F[:8])

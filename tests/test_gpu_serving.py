@@ -254,6 +254,34 @@ def test_served_equals_alone(gt, stream_ds):
         alone.close()
 
 
+def test_server_refuses_bad_insert_rows_when_queued(gt, stream_ds):
+    # rows are checked when they are queued (a step then applies them without
+    # waiting for the device): a negative or non-finite entry is refused at
+    # once and nothing of that call is queued
+    ds = stream_ds
+    t = gt.Tree(ds.F[:1000], capacity=2000)
+    srv = gt.Server(t, dtype="bf16")
+    for bad in (-1e-3, np.nan, np.inf):
+        row = ds.F[1000:1002].copy()
+        row[1, 5] = bad
+        with pytest.raises(gt.GTError) as e:
+            srv.insert(row)
+        assert e.value.status == 2
+    srv.insert(ds.F[1000:1002])
+    srv.submit(ds.Q[:4], ds.rho[:4], np.arange(4))
+    got = {}
+    for _ in range(8):
+        srv.step()
+        for tag, ids, snap in srv.poll():
+            got[tag] = (ids, snap)
+    srv.close()
+    ref = oracle.brute_force(ds.F[:1002], ds.Q[:4], ds.rho[:4])
+    for i in range(4):
+        assert got[i][1] == 1002
+        assert np.array_equal(got[i][0], ref.neighbours(i))
+    t.close()
+
+
 def test_server_without_inserts_matches_batch_query(gt, stream_ds):
     ds = stream_ds
     t = gt.Tree(ds.F)
