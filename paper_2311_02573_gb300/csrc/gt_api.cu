@@ -738,12 +738,10 @@ static gt_status run_search_on(gt_tree *t, const float *Q, int64_t B, const floa
           launch_level_sub(t, fmt, h, reinterpret_cast<const SibPair *>(in), w.counters + h, outp,
                            w.counters + h - 1, s, items_sub);
         } else if (sub && items_sub) {
-          // the items: right items decided with the left items' bounds, then
-          // the left items that the bound keeps
-          launch_items_sub(t, fmt, reinterpret_cast<const SibPair *>(in), w.counters, w.front[1],
+          // the items: right items decided, left items by their bounds or,
+          // when those straddle rho, from their rows in the same launch
+          launch_items_sub(t, fmt, reinterpret_cast<const SibPair *>(in), w.counters,
                            w.counters + kLeftItemsSlot, s);
-          launch_level(t, fmt, 0, q0, w.front[1], w.counters + kLeftItemsSlot, nullptr, nullptr, s);
-          n_launch += 1;
         } else {
           launch_level(t, fmt, h, q0, in, w.counters + h, outp, h > 0 ? w.counters + h - 1 : nullptr, s);
         }
@@ -752,7 +750,7 @@ static gt_status run_search_on(gt_tree *t, const float *Q, int64_t B, const floa
         if (h > 0) n_level += 1;
       }
       if (drain && defer_active(t, fmt)) n_launch += 1;
-      if (first_level >= 0 && defer_active(t, fmt)) n_launch += (sub && items_sub) ? 2 : 1;
+      if (first_level >= 0 && defer_active(t, fmt)) n_launch += 1;
       tmr.begin(3);
       launch_recheck(t, q0, s);
       tmr.end();

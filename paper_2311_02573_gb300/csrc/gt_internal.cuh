@@ -241,7 +241,7 @@ void launch_root(gt_tree *t, int64_t q0, int64_t b, Pair *out, uint32_t *count, 
 // Subtraction at the items: entries (q, c, U) of level-1 pools c in; the
 // right item 2c+1 is decided (results, rechecks), the left item 2c is written
 // to `left` as a leaf pair when its bound U - L_right reaches rho.
-void launch_items_sub(gt_tree *t, int fmt, const SibPair *in, const uint32_t *in_count, Pair *left,
+void launch_items_sub(gt_tree *t, int fmt, const SibPair *in, const uint32_t *in_count,
                       uint32_t *left_count, cudaStream_t s);
 bool items_sub_available(gt_tree *t, int fmt);
 // Counter slot of the leaf pairs that the subtraction at the items passes on

@@ -72,7 +72,7 @@ struct gt_server {
   float *ins_h = nullptr, *ins_d = nullptr;
   int64_t ins_cap = 0, ins_n = 0;
   // subtraction path (entries of 16 bytes in the level lists) and the
-  // subtraction at the items (left items in `left`)
+  // subtraction at the items
   bool sub = false, items_sub = false;
   // prefix layout: list h holds entries of level-(h+1) pools (16 bytes, as
   // on the subtraction path), each split at its midpoint by one prefix row
@@ -91,7 +91,6 @@ struct gt_server {
   // per level two lists (parity), results, rechecks, counters, flags
   gt::Pair *lists[gt::kMaxCut][2] = {};
   gt::Pair *gemm_out = nullptr;  // the new group's GEMM survivors before grouping by query
-  gt::Pair *left = nullptr;      // left items kept by the subtraction at the items
   int64_t *bcnt = nullptr, *boff = nullptr;  // grouping by query: counts, offsets
   gt::Pair *res = nullptr, *rchk = nullptr;
   int64_t res_cap = 0, rchk_cap = 0;
@@ -188,7 +187,6 @@ gt_status server_alloc(gt_server *S) {
   for (int h = 0; h < S->cut; ++h)
     for (int p = 0; p < 2; ++p) GT_CUDA(cudaMalloc(&S->lists[h][p], (size_t)S->list_cap * sizeof(Pair)));
   GT_CUDA(cudaMalloc(&S->gemm_out, (size_t)S->list_cap * sizeof(Pair)));
-  GT_CUDA(cudaMalloc(&S->left, (size_t)S->list_cap * sizeof(Pair)));
   GT_CUDA(cudaMalloc(&S->bcnt, (size_t)(S->slots + 1) * sizeof(int64_t)));
   GT_CUDA(cudaMalloc(&S->boff, (size_t)(S->slots + 1) * sizeof(int64_t)));
   GT_CUDA(cudaMalloc(&S->res, (size_t)S->res_cap * sizeof(Pair)));
@@ -230,7 +228,7 @@ void server_release(gt_server *S) {
   cudaFree(S->ins_d);
   for (int h = 0; h < kMaxCut; ++h)
     for (int p = 0; p < 2; ++p) cudaFree(S->lists[h][p]);
-  cudaFree(S->gemm_out); cudaFree(S->left); cudaFree(S->bcnt); cudaFree(S->boff);
+  cudaFree(S->gemm_out); cudaFree(S->bcnt); cudaFree(S->boff);
   cudaFree(S->drain_buf);
   cudaFree(S->res); cudaFree(S->rchk); cudaFree(S->counters);
   if (S->hcounters) cudaFreeHost(S->hcounters);
@@ -621,11 +619,9 @@ gt_status gt_server_step(gt_server *S, int64_t *in_flight) {
                        S->counters + 2 * h + p, S->lists[h - 1][np], S->counters + 2 * (h - 1) + np, s,
                        S->items_sub);
     } else if (S->items_sub) {
-      // right items decided with the left items' bounds, then the left items kept
+      // right items decided, left items by their bounds or from their rows
       launch_items_sub(&v, S->fmt, reinterpret_cast<const SibPair *>(S->lists[0][p]), S->counters + p,
-                       S->left, S->counters + kLeftItemsSlot, s);
-      launch_level(&v, S->fmt, 0, 0, S->left, S->counters + kLeftItemsSlot, nullptr, nullptr, s);
-      ++launches;
+                       S->counters + kLeftItemsSlot, s);
     } else {
       launch_level(&v, S->fmt, h, 0, S->lists[h][p], S->counters + 2 * h + p,
                    h > 0 ? S->lists[h - 1][np] : nullptr, h > 0 ? S->counters + 2 * (h - 1) + np : nullptr,
@@ -713,7 +709,6 @@ gt_status gt_server_step(gt_server *S, int64_t *in_flight) {
   bool fresh_overflow = b > 0 && fresh_pairs > fresh_lim;
   if (hc[64 + kFlagOverflow]) {
     bool older = hc[kMaxLevels] > (uint32_t)S->res_cap || hc[kMaxLevels + 1] > (uint32_t)S->rchk_cap;
-    older |= hc[kLeftItemsSlot] > (uint32_t)S->list_cap;
     for (int h = 0; h + 1 < cut; ++h) older |= hc[2 * h + np] > (uint32_t)list_entries(S);
     if (older) return set_error(GT_EOVERFLOW, "a query group outgrew the server's frontier budget");
     fresh_overflow = b > 0;

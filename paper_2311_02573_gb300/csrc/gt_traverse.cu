@@ -779,9 +779,10 @@ __device__ __forceinline__ void ring_copy(uint32_t dst, const void *src, uint32_
 // results and rechecks out); 2: subtraction level (entries in and out); 3:
 // subtraction into the leaves (entries in, item pairs out); 4: subtraction
 // at the items (entries of level-1 pools in: the right item is decided like
-// a leaf, results and rechecks out, and the left item, bounded by the pool's
-// bound minus the right item's lower bound, is passed on as a leaf pair when
-// that bound reaches rho); 5: prefix split (entries {q, pool, prefix score at
+// a leaf, results and rechecks out; the left item is accepted on its lower
+// bound, the pool's minus the right item's upper bound, or else, while its
+// upper bound reaches rho, gathered and decided like a leaf in the same
+// launch); 5: prefix split (entries {q, pool, prefix score at
 // the pool's start, at its end} in, the kept children out as entries); 6:
 // prefix split of level-1 pools (both items decided: results and rechecks
 // out).  In modes 5 and 6 the gathered row is the prefix row that ends at the
@@ -934,6 +935,8 @@ __global__ void __launch_bounds__(32 * kRingWarps, 1)
     uint32_t m_c = 0;            // MODE 4: the left item is tested next
     uint32_t m_d = 0;            // FP8 leaves: re-scored by the BF16 pass
     uint32_t m_e = 0;            // MODE 4: the left item accepted on its lower bound
+    uint32_t m_la = 0, m_lr = 0, m_ld = 0;  // MODE 4: the left item tested from its row:
+                                            // accepted, FP64 recheck, BF16 re-score
     float my_ul = 0.f, my_ur = 0.f, my_ll = 0.f, my_lr = 0.f;
     // At the pool levels (modes 0, 2, 3, 5) the per-pair loop only gathers
     // and scores: wait for the row, dot product, refill the slot, warp sum.
@@ -1136,6 +1139,29 @@ __global__ void __launch_bounds__(32 * kRingWarps, 1)
       const bool al = mine && !a.no_accept && Ll >= rho_4;
       m_e = __ballot_sync(FULL, al);
       m_c = __ballot_sync(FULL, mine && !al && Ul >= rho_4);
+      // the left items whose bounds straddle rho (a few per batch) are
+      // gathered and decided here, warp-wide, one at a time, like any leaf:
+      // no list and no launch of their own
+      uint32_t need = m_c;
+      while (need) {
+        const int j = __ffs(need) - 1;
+        need &= need - 1u;
+        const uint32_t qj = __shfl_sync(FULL, e_cur.q, j);
+        const uint32_t item = 2u * __shfl_sync(FULL, e_cur.p, j);
+        if (qj != cur_q) load_query(qj);
+        const uint8_t *row = a.rows + (size_t)item * a.row_bytes;
+        uint4 w[KV];
+#pragma unroll
+        for (int kk = 0; kk < KV; ++kk) {
+          const int v = lane + 32 * kk;
+          w[kk] = v < a.nvec ? ld_stream(row + 16 * v) : make_uint4(0u, 0u, 0u, 0u);
+        }
+        const float acc = warp_sum(row_dot<FMT, KV, false>(w, qreg, nullptr, a.nvec));
+        decide<FMT, KV, true, false>(a, acc, item, qn1, rho, qreg, nullptr, j, m_la, m_lr, m_ld,
+                                     n_refine);
+      }
+      // (counted with the tests, as left items)
+      if (m_c && lane == 0) atomicAdd(a.out_count, (uint32_t)__popc(m_c));
     }
     if (PRE) {
       my_ul = my_acc;
@@ -1219,13 +1245,17 @@ __global__ void __launch_bounds__(32 * kRingWarps, 1)
       Pair right, left;
       right.q = pr.q; right.j = 2u * pr.j + 1u;
       left.q = pr.q; left.j = 2u * pr.j;
-      const bool ar = (m_a >> lane) & 1u, al = (m_e >> lane) & 1u;
+      const bool ar = (m_a >> lane) & 1u, al = ((m_e | m_la) >> lane) & 1u;
       warp_append(a.res, a.res_count, a.res_cap, a.flags, (ar ? 1u : 0u) + (al ? 1u : 0u),
                   ar ? right : left, left);
-      warp_append(a.rchk, a.rchk_count, a.rchk_cap, a.flags, (m_b >> lane) & 1u, right, right);
-      if (FMT == GT_FP8 && m_d)
-        warp_append(a.defer, a.defer_count, a.defer_cap, a.flags, (m_d >> lane) & 1u, right, right);
-      warp_append(a.out, a.out_count, a.out_cap, a.flags, (m_c >> lane) & 1u, left, left);
+      const bool cr = (m_b >> lane) & 1u, cl = (m_lr >> lane) & 1u;
+      warp_append(a.rchk, a.rchk_count, a.rchk_cap, a.flags, (cr ? 1u : 0u) + (cl ? 1u : 0u),
+                  cr ? right : left, left);
+      if (FMT == GT_FP8 && (m_d | m_ld)) {
+        const bool dr = (m_d >> lane) & 1u, dl = (m_ld >> lane) & 1u;
+        warp_append(a.defer, a.defer_count, a.defer_cap, a.flags, (dr ? 1u : 0u) + (dl ? 1u : 0u),
+                    dr ? right : left, left);
+      }
     } else if (MODE == 5) {
       pre_emit(a, out_v, e_cur, m_a, m_b, my_ul);
     } else if (MODE == 6) {
@@ -2749,7 +2779,7 @@ void launch_level_sub(gt_tree *t, int fmt, int h, const SibPair *in, const uint3
   }
 }
 
-void launch_items_sub(gt_tree *t, int fmt, const SibPair *in, const uint32_t *in_count, Pair *left,
+void launch_items_sub(gt_tree *t, int fmt, const SibPair *in, const uint32_t *in_count,
                       uint32_t *left_count, cudaStream_t s) {
   Workspace &w = t->ws;
   LevelArgs a;
@@ -2771,9 +2801,9 @@ void launch_items_sub(gt_tree *t, int fmt, const SibPair *in, const uint32_t *in
   a.rho = w.rho;
   a.in_count = in_count;
   a.in_cap = (uint32_t)(w.front_lim / 2);
-  a.out = left;
-  a.out_count = left_count;
-  a.out_cap = (uint32_t)w.front_lim;
+  a.out = nullptr;              // the left items are decided in the launch;
+  a.out_count = left_count;     // their count is kept with the tests
+  a.out_cap = 0;
   a.res = w.res;
   a.res_count = w.counters + kMaxLevels;
   a.res_cap = (uint32_t)std::min<int64_t>(w.res_cap, 0xffffffffLL);
