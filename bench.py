@@ -78,6 +78,9 @@ def _args():
                    help="skip the large form (N = 10M, FP8 rows, 100,000 queries)")
     p.add_argument("--serve-rates", default="50000,400000,0",
                    help="offered request rates for the serving run (0: all at once)")
+    p.add_argument("--serve-groups", type=int, default=0,
+                   help="also time server steps that each answer a fixed group of this many "
+                        "queries (no arrival clock: for profiling one served step)")
     return p.parse_args()
 
 
@@ -291,6 +294,28 @@ def serve_run(gt, tree, Q, rhos, rate, n_req, dtype, inserts=None, insert_frac=0
             "cutover": st["cutover"], "launches": st["launches"],
             "schedule": {1: "levels", 2: "drain", 3: "immediate"}.get(st["schedule"], st["schedule"])}
 
+
+
+def serve_fixed_groups(gt, tree, Q, rho, group, dtype, steps=60, warm=10):
+    """Server steps that each admit and answer one group of `group` queries
+    (the default schedule), with no arrival clock: the host wall time of a
+    step (gt_server_step, synchronize included), median over the steps after
+    the first `warm`."""
+    srv = gt.Server(tree, dtype=dtype)
+    B = Q.shape[0]
+    times = []
+    for i in range(steps):
+        lo = (i * group) % max(1, B - group)
+        srv.submit(Q[lo:lo + group], rho, np.arange(lo, lo + group))
+        t0 = time.perf_counter()
+        srv.step()
+        times.append(time.perf_counter() - t0)
+        srv.poll_arrays()
+    st = srv.stats()
+    srv.close()
+    return {"group": group, "steps": steps, "step_ms_median": round(1e3 * float(np.median(times[warm:])), 4),
+            "schedule": {1: "levels", 2: "drain", 3: "immediate"}.get(st["schedule"], st["schedule"]),
+            "launches_per_step": round(st["launches"] / max(1, st["steps"]), 2)}
 
 
 def side_by_side(gt, tree, Fd, Qd, rd, B, dtype, tune, flush, capacity, reps=3):
@@ -982,6 +1007,9 @@ def main():
                                  "decisions_outside_its_rounding_bound": int(ref.ambiguous.sum())}}
 
     # the serving run inserts rows, so it comes after every exactness check
+    served_fixed = None
+    if a.serve_groups > 0 and rank == 0:
+        served_fixed = serve_fixed_groups(gt, tree, Q, float(a.rho), a.serve_groups, a.dtype)
     serving = None
     if not a.no_serve and rank == 0:
         rhos = np.array(ds.workload.rhos or (a.rho,), dtype=np.float32)
@@ -1055,6 +1083,7 @@ def main():
             "comparators": comparators,
             "serving": serving,
             "served_n1m_d512": served_d512,
+            "served_fixed_groups": served_fixed,
             "large_n10m_fp8": large,
             "streaming": streaming,
             "parity_sample": parity,

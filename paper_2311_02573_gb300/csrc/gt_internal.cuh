@@ -29,6 +29,10 @@ constexpr int kMaxLevels = 40;
 // counter slots after the levels: [40] results, [41] rechecks, [42] refines,
 // [43] segments left for the block sort of the CSR assembly
 constexpr int kCsrListSlot = kMaxLevels + 3;
+// CSR assembly (launch_csr_into) of at most this many queries runs in one
+// block, which writes only the offsets and ids it is given (host-mapped
+// buffers included)
+constexpr int kCsrSmallMax = 64;
 constexpr int kWarp = 32;
 
 // Device-side status words (one array per tree, cleared per call).

@@ -358,20 +358,32 @@ gt_status step_immediate(gt_server *S, int64_t *in_flight) {
     }
     launch_drain(&v, S->fmt, cut, queue, gemm_count, s, S->counters + kDrainCounts,
                  S->counters + kDrainCounts + 8);
-    launch_recheck(&v, 0, s, b <= kUngroupedMax ? t->sm_count : 0);
-    GT_CUDA(cudaMemsetAsync(S->cnt + s0, 0, (size_t)(b + 1) * sizeof(int64_t), s));
-    launch_csr_into(&v, S->res, (uint32_t)S->res_cap, S->counters + kMaxLevels, s0, b, S->cnt, S->off,
-                    S->ids, S->counters + kCsrListSlot, s);
-    GT_CUDA(cudaMemcpyAsync(S->hoff, S->off + s0, (size_t)(b + 1) * sizeof(int64_t),
-                            cudaMemcpyDeviceToHost, s));
-    const int64_t ids_pre = std::min<int64_t>(S->ids_guess, S->hids_cap);
-    GT_CUDA(cudaMemcpyAsync(S->hids, S->ids, (size_t)ids_pre * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    launch_recheck(&v, 0, s, b <= kUngroupedMax ? 16 : 0);
+    // a small group's CSR (one block) writes its offsets and ids straight
+    // into the page-locked host buffers (mapped into the device's address
+    // space), so they need no copy; a large group's is copied out (its ids
+    // in part, by a guess, the rest after the synchronize when the guess was
+    // short)
+    const bool small = b <= kCsrSmallMax;
+    int64_t ids_pre = S->hids_cap;
+    if (small) {
+      launch_csr_into(&v, S->res, (uint32_t)S->res_cap, S->counters + kMaxLevels, s0, b, S->cnt, S->hoff,
+                      S->hids, S->counters + kCsrListSlot, s);
+    } else {
+      GT_CUDA(cudaMemsetAsync(S->cnt + s0, 0, (size_t)(b + 1) * sizeof(int64_t), s));
+      launch_csr_into(&v, S->res, (uint32_t)S->res_cap, S->counters + kMaxLevels, s0, b, S->cnt, S->off,
+                      S->ids, S->counters + kCsrListSlot, s);
+      GT_CUDA(cudaMemcpyAsync(S->hoff, S->off + s0, (size_t)(b + 1) * sizeof(int64_t),
+                              cudaMemcpyDeviceToHost, s));
+      ids_pre = std::min<int64_t>(S->ids_guess, S->hids_cap);
+      GT_CUDA(cudaMemcpyAsync(S->hids, S->ids, (size_t)ids_pre * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    }
     GT_CUDA(cudaGetLastError());
     GT_CUDA(cudaMemcpyAsync(S->hcounters, S->counters, 128 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     GT_CUDA(cudaStreamSynchronize(s));
     // reset, prep, thresholds, GEMM, drain, recheck, and the CSR's (one block
-    // and its long-segment sort for a small group)
-    launches += 6 + (b <= 64 ? 2 : 6);
+    // for a small group)
+    launches += 6 + (small ? 1 : 6);
     const uint32_t *hc = S->hcounters;
     st = step_flags(S, hc);
     if (st != GT_OK) return st;

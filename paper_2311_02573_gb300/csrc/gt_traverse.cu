@@ -2065,23 +2065,23 @@ __global__ void __launch_bounds__(256) k_csr_sort_warp(const int64_t *off, int32
 
 // The CSR of a few queries (B <= kCsrSmallMax) in one block: counts per query
 // in shared memory, their scan, the fill (ids through the tree permutation)
-// and the sort of each query's ids by one warp; segments longer than a warp
-// sorts are listed for k_csr_sort.  One launch instead of the six of the
+// and the sort of each query's ids by one warp, or by the whole block for a
+// segment longer than a warp sorts.  One launch instead of the six of the
 // general passes: a served group's step is bound by such fixed costs.
-constexpr int kCsrSmallMax = 64;
-__global__ void __launch_bounds__(1024) k_csr_small(const Pair *res, uint32_t n_cap,
+__global__ void __launch_bounds__(1024, 1) k_csr_small(const Pair *res, uint32_t n_cap,
                                                     const uint32_t *n_dev, uint32_t q_lo,
                                                     uint32_t B, int64_t *off_r,
-                                                    const int32_t *perm, int32_t *ids,
-                                                    int64_t *list, uint32_t *list_n, int *flags) {
+                                                    const int32_t *perm, int32_t *ids, int *flags) {
   __shared__ uint32_t cnt[kCsrSmallMax + 1], cur[kCsrSmallMax + 1];
   __shared__ int64_t start[kCsrSmallMax + 1];
+  __shared__ uint32_t n_long, longq[kCsrSmallMax];
+  __shared__ int32_t buf[kSortSmem];
   const uint32_t tid = threadIdx.x;
   if (tid <= B) {
     cnt[tid] = 0u;
     cur[tid] = 0u;
   }
-  if (tid == 0) *list_n = 0u;
+  if (tid == 0) n_long = 0u;
   __syncthreads();
   const uint32_t n = csr_n(n_cap, n_dev);
   for (uint32_t i = tid; i < n; i += blockDim.x) {
@@ -2117,10 +2117,26 @@ __global__ void __launch_bounds__(1024) k_csr_small(const Pair *res, uint32_t n_
   for (uint32_t q = warp; q < B; q += blockDim.x >> 5) {
     const int64_t m = cnt[q];
     if (m > 512) {
-      if (lane == 0) list[atomicAdd(list_n, 1u)] = q;
+      if (lane == 0) longq[atomicAdd(&n_long, 1u)] = q;
     } else if (m > 1) {
       warp_sort_ids<16>(ids, start[q], m);
     }
+  }
+  __syncthreads();
+  // the long segments, by the whole block: in shared memory up to kSortSmem
+  // ids, in place in memory beyond
+  for (uint32_t e = 0; e < n_long; ++e) {
+    const uint32_t q = longq[e];
+    const int64_t s = start[q], m = cnt[q];
+    if (m <= kSortSmem) {
+      for (int64_t i = tid; i < m; i += blockDim.x) buf[i] = ids[s + i];
+      __syncthreads();
+      bitonic<true>(buf, m);
+      for (int64_t i = tid; i < m; i += blockDim.x) ids[s + i] = buf[i];
+    } else {
+      bitonic<false>(ids + s, m);
+    }
+    __syncthreads();
   }
 }
 
@@ -2874,11 +2890,9 @@ void launch_csr_into(gt_tree *t, const Pair *res, uint32_t n, const uint32_t *n_
   int64_t *cnt_r = cnt + q_lo, *off_r = off + q_lo;
   const uint32_t q_hi = (uint32_t)(q_lo + B);
   if (B >= 1 && B <= kCsrSmallMax) {
-    // one block for the CSR of a few queries; its long segments (listed in
-    // cnt_r, then unused) sorted after it
+    // one block for the CSR of a few queries
     k_csr_small<<<1, 1024, 0, s>>>(res, n, n_dev, (uint32_t)q_lo, (uint32_t)B, off_r, t->perm, ids,
-                                   cnt_r, list_n, t->flags);
-    k_csr_sort<<<(unsigned)B, 256, 0, s>>>(off_r, ids, cnt_r, list_n);
+                                   t->flags);
     return;
   }
   if (any) k_csr_count<<<blocks, 256, 0, s>>>(res, n, n_dev, (uint32_t)q_lo, q_hi, cnt, t->flags);
