@@ -101,8 +101,6 @@ void free_workspace(gt_tree *t) {
   cudaFree(w.qn1);
   cudaFree(w.rho);
   cudaFree(w.stage);
-  cudaFree(w.thr_keep);
-  cudaFree(w.thr_accept);
   cudaFree(w.bcnt);
   cudaFree(w.boff);
   cudaFree(w.drain);
@@ -697,7 +695,7 @@ static gt_status run_search_on(gt_tree *t, const float *Q, int64_t B, const floa
         gt_status e = launch_dense(t, 0, 1, q0, b, nullptr, nullptr, s);
         tmr.end();
         if (e != GT_OK) return e;
-        n_launch += 2;  // thresholds + GEMM
+        n_launch += 1;  // GEMM
         first_level = -1;  // the GEMM epilogue decided every item
       } else {
         tmr.begin(2);
@@ -710,7 +708,7 @@ static gt_status run_search_on(gt_tree *t, const float *Q, int64_t B, const floa
         launch_bucket(t, sub, w.front[cut & 1], w.front[(cut - 1) & 1], w.counters + (cut - 1),
                       (uint32_t)(sub ? w.front_lim / 2 : w.front_lim), q0, b, s);
         tmr.end();
-        n_launch += 6;  // thresholds + GEMM + count, scan, scatter, count fix
+        n_launch += 5;  // GEMM + count, scan, scatter, count fix
         first_level = cut - 1;
       }
       if (drain) {
@@ -770,7 +768,7 @@ static gt_status run_search_on(gt_tree *t, const float *Q, int64_t B, const floa
     key.q0 = q0; key.b = b; key.N = t->N; key.front_lim = w.front_lim;
     key.res_cap = w.res_cap; key.rchk_cap = w.rchk_cap;
     const void *ptrs[] = {w.front[0], w.front[1], w.res, w.rchk, w.counters, w.hcounters, w.qf32,
-                          w.qbf16, w.qn1, w.rho, w.thr_keep, w.thr_accept, w.bcnt, w.boff, w.defer,
+                          w.qbf16, w.qn1, w.rho, w.bcnt, w.boff, w.defer,
                           t->rows32, t->rows16, t->rows8, t->scale8, t->perm, t->flags, s,
                           t->pref16, t->pref32};
     static_assert(sizeof(ptrs) / sizeof(ptrs[0]) <= sizeof(key.p) / sizeof(key.p[0]), "key");

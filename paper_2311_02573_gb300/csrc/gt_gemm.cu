@@ -67,8 +67,11 @@ struct DenseArgs {
   uint32_t q0, nq;     // queries [q0, q0 + nq)
   int k_blocks;
   uint32_t n_child;    // rows at level h-1 (mode 0)
-  const float *thr_keep;    // per query: keep / candidate iff acc >= thr_keep[q]
-  const float *thr_accept;  // per query: accept iff acc >= thr_accept[q] (mode 1)
+  const float *rho;    // per query threshold; the epilogue keeps (or, for mode
+                       // 0 and 3, takes as a candidate) a pool when acc >=
+                       // rho * inv_cu rounded down, and accepts an item (mode 1)
+                       // when acc >= rho * inv_cl rounded up
+  float inv_cu, inv_cl;
   Pair *out;
   uint32_t *out_count;
   uint32_t out_cap;
@@ -272,8 +275,9 @@ __device__ __forceinline__ void epilogue_tile(const DenseArgs &a, uint32_t tcol,
                                               uint32_t col0) {
   const bool qvalid = row < a.nq;
   const uint32_t q = a.q0 + row;
-  const float keep = qvalid ? a.thr_keep[q] : INFINITY;
-  const float accept = (qvalid && a.mode == 1) ? a.thr_accept[q] : INFINITY;
+  const float r = qvalid ? a.rho[q] : 0.f;
+  const float keep = qvalid ? __fmul_rd(r, a.inv_cu) : INFINITY;
+  const float accept = (qvalid && a.mode == 1) ? __fmul_ru(r, a.inv_cl) : INFINITY;
 #pragma unroll 1
   for (int c = 0; c < BN / 64; ++c) {
     uint32_t r[64];
@@ -845,18 +849,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Pair2::THREADS, 1)
   }
 }
 
-// Per-query thresholds on the raw accumulator for level h: the pool is kept
-// when acc * cu >= rho (cu bounds the exact score from above), accepted at
-// level 0 when acc * cl >= rho.  Rounded so the comparison stays rigorous.
-__global__ void k_thresholds(const float *rho, int64_t q0, int64_t b, float inv_cu, float inv_cl,
-                             float *keep, float *accept) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= b) return;
-  const float r = rho[q0 + i];
-  keep[q0 + i] = __fmul_rd(r, inv_cu);
-  accept[q0 + i] = __fmul_ru(r, inv_cl);
-}
-
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
@@ -948,16 +940,18 @@ gt_status launch_dense_impl(gt_tree *t, int h, int mode, int64_t q0, int64_t b, 
   Workspace &w = t->ws;
   if (!dense_available()) return set_error(GT_EINVAL, "dense GEMM path not available");
   if (!t->rows16) return set_error(GT_EINVAL, "dense GEMM needs BF16 rows");
-  if (!w.thr_keep || w.thr_cap < b + q0)
-    return set_error(GT_EINVAL, "dense GEMM thresholds were not reserved with the queries");
+  if (!w.rho || w.q_cap < b + q0)
+    return set_error(GT_EINVAL, "dense GEMM queries were not reserved");
   double cu, cl;
   gemm_bound(bound_level(t, h), &cu, &cl);
-  // 1/cu rounded down, 1/cl rounded up (then the kernel rounds the products)
+  // The epilogue's per-query thresholds on the raw accumulator: a pool is kept
+  // when acc * cu >= rho (cu bounds the exact score from above), an item
+  // accepted when acc * cl >= rho; as acc >= rho * (1/cu) and acc >= rho *
+  // (1/cl), with 1/cu rounded down and 1/cl rounded up here and the products
+  // rounded the same ways in the kernel, so the comparisons stay rigorous.
   float inv_cu = (float)(1.0 / cu), inv_cl = (float)(1.0 / cl);
   if ((double)inv_cu > 1.0 / cu) inv_cu = std::nextafter(inv_cu, 0.0f);
   if ((double)inv_cl < 1.0 / cl) inv_cl = std::nextafter(inv_cl, INFINITY);
-  k_thresholds<<<(unsigned)((b + 255) / 256), 256, 0, s>>>(w.rho, q0, b, inv_cu, inv_cl,
-                                                           w.thr_keep, w.thr_accept);
   const int64_t rows = level_rows(t->N, h);
   CUtensorMap mq, mp;
   if (!make_map(&mq, w.qbf16, (uint64_t)w.q_cap, (uint64_t)t->stride, (uint64_t)t->stride * 2, BM))
@@ -977,8 +971,9 @@ gt_status launch_dense_impl(gt_tree *t, int h, int mode, int64_t q0, int64_t b, 
   a.nq = (uint32_t)b;
   a.k_blocks = (int)(t->stride / BK);
   a.n_child = h > 0 ? (uint32_t)level_rows(t->N, h - 1) : 0u;
-  a.thr_keep = w.thr_keep;
-  a.thr_accept = w.thr_accept;
+  a.rho = w.rho;
+  a.inv_cu = inv_cu;
+  a.inv_cl = inv_cl;
   if (mode == 1) {
     a.out = w.res;
     a.out_count = w.counters + kMaxLevels;

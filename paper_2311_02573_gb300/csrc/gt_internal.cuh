@@ -106,9 +106,6 @@ struct Workspace {
   float *qn1 = nullptr;          // per-query upper bound on |q|_1
   float *rho = nullptr;          // per-query thresholds
   int64_t q_cap = 0;
-  float *thr_keep = nullptr;     // GEMM path: per-query accumulator thresholds
-  float *thr_accept = nullptr;
-  int64_t thr_cap = 0;
   int64_t *bcnt = nullptr;       // per-query counts / cursors of the bucketing pass
   int64_t *boff = nullptr;       // per-query offsets of the bucketing pass
   float *stage = nullptr;        // host->device staging of inputs
@@ -286,9 +283,12 @@ gt_status ws_reserve_drain(gt_tree *t);
 // GEMM's level-(cut-1) entries (grouped by query), `root_count` their count.
 // The entries tested at each level h < cut - 1 are added to level_count[h]
 // and the left items tested to *left_count (null: the workspace's level
-// counters and its left-item slot).
+// counters and its left-item slot).  `cleared`: the caller has zeroed the
+// queue head (kDrainHeadSlot) and the deferred-pair count (kDeferSlot) of the
+// workspace's counters already, in stream order before this launch.
 void launch_drain(gt_tree *t, int fmt, int cut, const SibPair *root, const uint32_t *root_count,
-                  cudaStream_t s, uint32_t *level_count = nullptr, uint32_t *left_count = nullptr);
+                  cudaStream_t s, uint32_t *level_count = nullptr, uint32_t *left_count = nullptr,
+                  bool cleared = false);
 // Kernel attributes of the level kernels, set once before any stream capture.
 void prepare_level_kernels();
 void launch_level(gt_tree *t, int fmt, int h, int64_t q0, const Pair *in, const uint32_t *in_count,
@@ -308,7 +308,7 @@ void gemm_bound(int h, double *cu, double *cl);
 // the ring-fed gather's slots do not fit rows of this format and width.
 bool launch_prefix(gt_tree *t, int fmt, int h, const SibPair *in, const uint32_t *in_count,
                    SibPair *out, uint32_t *out_count, cudaStream_t s);
-void launch_recheck(gt_tree *t, int64_t q0, cudaStream_t s, int max_blocks = 0);
+void launch_recheck(gt_tree *t, int64_t q0, cudaStream_t s);
 // The level kernels' test of n given (query, pool) pairs at level h: score,
 // upper and lower bound per pair into out (gt_pair_bounds).
 void launch_pair_bounds(gt_tree *t, int fmt, int h, const int32_t *pairs, int64_t n, int64_t n_queries,
@@ -316,10 +316,12 @@ void launch_pair_bounds(gt_tree *t, int fmt, int h, const int32_t *pairs, int64_
 // CSR assembly (see gt_traverse.cu) of the results of queries [q_lo, q_lo +
 // B): cnt (zero on entry) and off are indexed by query, so off[q_lo ..
 // q_lo + B] receives the offsets; n_dev, when given, is the device-side
-// result count (clamped to n)
+// result count (clamped to n).  With `recheck` the FP64 recheck of the
+// tree view's recheck list runs first (for at most kCsrSmallMax queries in
+// the same launch as the CSR), appending to `res` with the count at n_dev.
 void launch_csr_into(gt_tree *t, const Pair *res, uint32_t n, const uint32_t *n_dev, int64_t q_lo,
                      int64_t B, int64_t *cnt, int64_t *off, int32_t *ids, uint32_t *list_n,
-                     cudaStream_t s);
+                     cudaStream_t s, bool recheck = false);
 
 // dense tensor-core GEMM with a threshold epilogue (gt_gemm.cu)
 // mode 0: cutover - survivors' children at level h-1 go to `out`/`out_count`

@@ -60,7 +60,7 @@ struct gt_server {
   int64_t list_cap = 0;    // pairs per level list
   int64_t queue_cap = 0;   // initial arrival-queue capacity (queries)
   // query bank (device)
-  float *qf32 = nullptr, *qn1 = nullptr, *rho = nullptr, *thr_keep = nullptr, *thr_acc = nullptr;
+  float *qf32 = nullptr, *qn1 = nullptr, *rho = nullptr;
   __nv_bfloat16 *qbf16 = nullptr;
   float *stage = nullptr;  // device staging of one group's raw queries + rho
   // arrival queue: a ring of pinned host rows (admission copies straight from it)
@@ -121,15 +121,18 @@ namespace {
 
 // A view of the tree whose workspace points at the server's buffers.
 // Start of a step: the next-parity list counts of levels 0 .. cut-1, the
-// result, recheck and refine counts, the left-item count, the flags (words
-// 64 ..) and k_drain's test counts (words kDrainCounts ..) start at zero; the
-// current parity's counts are kept.
+// result, recheck and refine counts, the left-item count, k_drain's queue
+// head, the deferred FP8 pairs' count, the flags (words 64 ..) and k_drain's
+// test counts (words kDrainCounts ..) start at zero; the current parity's
+// counts are kept.
 constexpr int kDrainCounts = 96;  // k_drain: [96 + h] tests at level h, [96 + 8] left items
 __global__ void k_step_reset(uint32_t *counters, int np, int cut) {
   const int i = threadIdx.x;
   if (i < cut) counters[2 * i + np] = 0u;
   if (i < 3) counters[kMaxLevels + i] = 0u;
   if (i == 0) counters[kLeftItemsSlot] = 0u;
+  if (i == 1) counters[kDrainHeadSlot] = 0u;  // k_drain's queue head and
+  if (i == 2) counters[kDeferSlot] = 0u;      // deferred FP8 pairs
   if (i < kFlagCount) counters[64 + i] = 0u;
   if (i < 9) counters[kDrainCounts + i] = 0u;
 }
@@ -145,9 +148,6 @@ gt_tree view_of(gt_server *S, int64_t n_snap, int64_t slot0) {
   w.qn1 = S->qn1 + slot0;
   w.rho = S->rho + slot0;
   w.q_cap = S->slots - slot0;
-  w.thr_keep = S->thr_keep + slot0;
-  w.thr_accept = S->thr_acc + slot0;
-  w.thr_cap = w.q_cap;
   w.front_cap = S->list_cap;
   w.front_lim = S->list_cap;
   w.res = S->res;
@@ -172,8 +172,6 @@ gt_status server_alloc(gt_server *S) {
   GT_CUDA(cudaMalloc(&S->qbf16, (size_t)S->slots * st * sizeof(__nv_bfloat16)));
   GT_CUDA(cudaMalloc(&S->qn1, (size_t)S->slots * sizeof(float)));
   GT_CUDA(cudaMalloc(&S->rho, (size_t)S->slots * sizeof(float)));
-  GT_CUDA(cudaMalloc(&S->thr_keep, (size_t)S->slots * sizeof(float)));
-  GT_CUDA(cudaMalloc(&S->thr_acc, (size_t)S->slots * sizeof(float)));
   // staging and queues hold the caller's rows (d_in entries: a GT_POOL_MAXMIN
   // tree stores them split, 2 d_in wide)
   GT_CUDA(cudaMalloc(&S->stage, (size_t)S->max_group * (S->t->d_in + 1) * sizeof(float)));
@@ -221,7 +219,7 @@ gt_status server_alloc(gt_server *S) {
 
 void server_release(gt_server *S) {
   cudaFree(S->qf32); cudaFree(S->qbf16); cudaFree(S->qn1); cudaFree(S->rho);
-  cudaFree(S->thr_keep); cudaFree(S->thr_acc); cudaFree(S->stage);
+  cudaFree(S->stage);
   if (S->ring_q) cudaFreeHost(S->ring_q);
   if (S->ring_rho) cudaFreeHost(S->ring_rho);
   if (S->ins_h) cudaFreeHost(S->ins_h);
@@ -357,19 +355,19 @@ gt_status step_immediate(gt_server *S, int64_t *in_flight) {
       launches += 4;
     }
     launch_drain(&v, S->fmt, cut, queue, gemm_count, s, S->counters + kDrainCounts,
-                 S->counters + kDrainCounts + 8);
-    launch_recheck(&v, 0, s, b <= kUngroupedMax ? 16 : 0);
-    // a small group's CSR (one block) writes its offsets and ids straight
-    // into the page-locked host buffers (mapped into the device's address
-    // space), so they need no copy; a large group's is copied out (its ids
-    // in part, by a guess, the rest after the synchronize when the guess was
-    // short)
+                 S->counters + kDrainCounts + 8, /*cleared=*/true);
+    // a small group's recheck and CSR run in one block, which writes the
+    // offsets and ids straight into the page-locked host buffers (mapped into
+    // the device's address space), so they need no copy; a large group's
+    // CSR is copied out (its ids in part, by a guess, the rest after the
+    // synchronize when the guess was short)
     const bool small = b <= kCsrSmallMax;
     int64_t ids_pre = S->hids_cap;
     if (small) {
       launch_csr_into(&v, S->res, (uint32_t)S->res_cap, S->counters + kMaxLevels, s0, b, S->cnt, S->hoff,
-                      S->hids, S->counters + kCsrListSlot, s);
+                      S->hids, S->counters + kCsrListSlot, s, /*recheck=*/true);
     } else {
+      launch_recheck(&v, 0, s);
       GT_CUDA(cudaMemsetAsync(S->cnt + s0, 0, (size_t)(b + 1) * sizeof(int64_t), s));
       launch_csr_into(&v, S->res, (uint32_t)S->res_cap, S->counters + kMaxLevels, s0, b, S->cnt, S->off,
                       S->ids, S->counters + kCsrListSlot, s);
@@ -381,9 +379,9 @@ gt_status step_immediate(gt_server *S, int64_t *in_flight) {
     GT_CUDA(cudaGetLastError());
     GT_CUDA(cudaMemcpyAsync(S->hcounters, S->counters, 128 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     GT_CUDA(cudaStreamSynchronize(s));
-    // reset, prep, thresholds, GEMM, drain, recheck, and the CSR's (one block
-    // for a small group)
-    launches += 6 + (small ? 1 : 6);
+    // reset, prep, GEMM, drain, then the recheck and the CSR's (one block
+    // for both for a small group)
+    launches += 4 + (small ? 1 : 7);
     const uint32_t *hc = S->hcounters;
     st = step_flags(S, hc);
     if (st != GT_OK) return st;
@@ -690,7 +688,7 @@ gt_status gt_server_step(gt_server *S, int64_t *in_flight) {
     // the GEMM's survivors grouped by query into the level-(c-1) list
     launch_bucket(&v, S->sub, S->gemm_out, S->lists[cut - 1][np], S->counters + 2 * (cut - 1) + np,
                   (uint32_t)list_entries(S), fresh_s0, b, s);
-    launches += 7;
+    launches += 6;  // prep, GEMM, bucketing (four)
   }
   GT_CUDA(cudaGetLastError());
   GT_CUDA(cudaMemcpyAsync(S->hcounters, S->counters, 128 * sizeof(uint32_t),

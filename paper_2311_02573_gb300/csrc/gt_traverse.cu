@@ -1700,37 +1700,46 @@ __global__ void __launch_bounds__(256) k_pair_bounds(const LevelArgs a, const in
 // Split signed rows (d_half > 0): the stored item and query rows are
 // [max(x, 0), max(-x, 0)], so x_j = row_j - row_{d_half + j} exactly, and the
 // recheck forms the signed q.f from those differences (exact FP64 products).
-__global__ void __launch_bounds__(256) k_recheck(const Pair *__restrict__ rchk,
-                                                 const uint32_t *count, uint32_t cap,
-                                                 const float *__restrict__ rows32,
-                                                 int64_t stride, int nv4, int d_half,
-                                                 const float *__restrict__ qf32,
-                                                 const float *__restrict__ rho, Pair *res,
-                                                 uint32_t *res_count, uint32_t res_cap,
-                                                 uint32_t q_lim, uint32_t n_items, int *flags) {
-  const int lane = threadIdx.x & 31;
-  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-  const uint32_t n = min(*count, cap);
+struct RecheckArgs {
+  const Pair *rchk;         // the doubtful (query, item) pairs and their count
+  const uint32_t *count;
+  uint32_t cap;
+  const float *rows32;      // FP32 item rows (row stride `stride`)
+  int64_t stride;
+  int nv4;                  // 16-byte vectors of an item row
+  int d_half;               // split signed rows: the caller's width, else 0
+  const float *qf32;
+  const float *rho;
+  Pair *res;                // accepted pairs are appended here
+  uint32_t *res_count;
+  uint32_t res_cap;
+  uint32_t q_lim, n_items;  // valid query slots and items (a corrupted entry is flagged)
+  int *flags;
+};
+
+// The pairs warp gw of nw takes: gw, gw + nw, ...
+__device__ __forceinline__ void recheck_pairs(const RecheckArgs &a, uint32_t gw, uint32_t nw,
+                                              int lane) {
+  const uint32_t n = min(*a.count, a.cap);
   for (uint32_t i = gw; i < n; i += nw) {
-    const Pair pr = rchk[i];
-    if (pr.q >= q_lim || pr.j >= n_items) {  // a corrupted list: flagged, left out
-      if (lane == 0) atomicExch(&flags[kFlagStray], 1);
+    const Pair pr = a.rchk[i];
+    if (pr.q >= a.q_lim || pr.j >= a.n_items) {  // a corrupted list: flagged, left out
+      if (lane == 0) atomicExch(&a.flags[kFlagStray], 1);
       continue;
     }
     double acc = 0.0;
-    if (d_half > 0) {
-      const float *f = rows32 + (size_t)pr.j * stride;
-      const float *qq = qf32 + (size_t)pr.q * stride;
-      for (int j = lane; j < d_half; j += 32) {
-        const double x = (double)f[j] - (double)f[d_half + j];
-        const double y = (double)qq[j] - (double)qq[d_half + j];
+    if (a.d_half > 0) {
+      const float *f = a.rows32 + (size_t)pr.j * a.stride;
+      const float *qq = a.qf32 + (size_t)pr.q * a.stride;
+      for (int j = lane; j < a.d_half; j += 32) {
+        const double x = (double)f[j] - (double)f[a.d_half + j];
+        const double y = (double)qq[j] - (double)qq[a.d_half + j];
         acc = fma(x, y, acc);
       }
     } else {
-      const float4 *f = reinterpret_cast<const float4 *>(rows32 + (size_t)pr.j * stride);
-      const float4 *qq = reinterpret_cast<const float4 *>(qf32 + (size_t)pr.q * stride);
-      for (int v = lane; v < nv4; v += 32) {
+      const float4 *f = reinterpret_cast<const float4 *>(a.rows32 + (size_t)pr.j * a.stride);
+      const float4 *qq = reinterpret_cast<const float4 *>(a.qf32 + (size_t)pr.q * a.stride);
+      for (int v = lane; v < a.nv4; v += 32) {
         const float4 x = f[v], y = qq[v];
         acc = fma((double)x.x, (double)y.x, acc);
         acc = fma((double)x.y, (double)y.y, acc);
@@ -1739,14 +1748,19 @@ __global__ void __launch_bounds__(256) k_recheck(const Pair *__restrict__ rchk,
       }
     }
     acc = warp_sum_d(acc);
-    if (lane == 0 && acc >= (double)rho[pr.q]) {
-      const uint32_t pos = atomicAdd(res_count, 1u);
-      if (pos < res_cap)
-        res[pos] = pr;
+    if (lane == 0 && acc >= (double)a.rho[pr.q]) {
+      const uint32_t pos = atomicAdd(a.res_count, 1u);
+      if (pos < a.res_cap)
+        a.res[pos] = pr;
       else
-        atomicExch(&flags[kFlagOverflow], 1);
+        atomicExch(&a.flags[kFlagOverflow], 1);
     }
   }
+}
+
+__global__ void __launch_bounds__(256) k_recheck(const RecheckArgs a) {
+  recheck_pairs(a, (blockIdx.x * blockDim.x + threadIdx.x) >> 5, (gridDim.x * blockDim.x) >> 5,
+                (int)(threadIdx.x & 31));
 }
 
 // Queries: pad to the row stride (FP32 and BF16), |q|_1 upper bound, domain
@@ -1761,25 +1775,40 @@ __global__ void __launch_bounds__(256) k_prep_queries(const float *__restrict__ 
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  constexpr int U = 8;  // loads a lane has in flight before it uses them
+  const int64_t n_in = split ? 2 * (int64_t)d : (int64_t)d;
   for (int64_t q = warp; q < B; q += nwarps) {
     const float *in = Q + q * (int64_t)d;
     float s = 0.f;
     bool bad = false;
-    for (int64_t j = lane; j < stride; j += 32) {
-      float x;
-      if (!split) {
-        x = j < d ? in[j] : 0.f;
-        bad |= !(x >= 0.f) || !isfinite(x);
-      } else if (j < 2 * (int64_t)d) {
-        const float y = in[j < d ? j : j - d];
-        bad |= !isfinite(y);
-        x = j < d ? (y > 0.f ? y : 0.f) : (y < 0.f ? -y : 0.f);
-      } else {
-        x = 0.f;
+    // a lane's entries j = lane, lane + 32, ... in that order (so the sum's
+    // rounding does not depend on U), read U at a time: for a small batch the
+    // kernel is one row per warp and waits on memory, not on arithmetic
+    for (int64_t j0 = lane; j0 < stride; j0 += 32 * U) {
+      float y[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t j = j0 + 32 * u;
+        y[u] = j < n_in ? in[j < d ? j : j - d] : 0.f;
       }
-      s += x;
-      qf32[q * stride + j] = x;
-      if (qbf16) qbf16[q * stride + j] = __float2bfloat16_rn(x);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t j = j0 + 32 * u;
+        if (j >= stride) break;
+        float x;
+        if (!split) {
+          x = y[u];
+          bad |= !(x >= 0.f) || !isfinite(x);
+        } else if (j < n_in) {
+          bad |= !isfinite(y[u]);
+          x = j < d ? (y[u] > 0.f ? y[u] : 0.f) : (y[u] < 0.f ? -y[u] : 0.f);
+        } else {
+          x = 0.f;
+        }
+        s += x;
+        qf32[q * stride + j] = x;
+        if (qbf16) qbf16[q * stride + j] = __float2bfloat16_rn(x);
+      }
     }
     s = warp_sum(s);
     if (__any_sync(FULL, bad) && lane == 0) atomicExch(&flags[kFlagDomain], 1);
@@ -2068,22 +2097,30 @@ __global__ void __launch_bounds__(256) k_csr_sort_warp(const int64_t *off, int32
 // and the sort of each query's ids by one warp, or by the whole block for a
 // segment longer than a warp sorts.  One launch instead of the six of the
 // general passes: a served group's step is bound by such fixed costs.
+//
+// With `recheck` the block first runs the FP64 recheck of the doubtful pairs
+// (a served group of a few queries has few of them), whose accepted pairs it
+// appends to the result list before counting it: the recheck and the CSR of a
+// small group in one launch.  The count is then read past the L1 cache, since
+// the recheck's appends updated it in L2.
 __global__ void __launch_bounds__(1024, 1) k_csr_small(const Pair *res, uint32_t n_cap,
                                                     const uint32_t *n_dev, uint32_t q_lo,
                                                     uint32_t B, int64_t *off_r,
-                                                    const int32_t *perm, int32_t *ids, int *flags) {
+                                                    const int32_t *perm, int32_t *ids, int *flags,
+                                                    const RecheckArgs rc, int recheck) {
   __shared__ uint32_t cnt[kCsrSmallMax + 1], cur[kCsrSmallMax + 1];
   __shared__ int64_t start[kCsrSmallMax + 1];
   __shared__ uint32_t n_long, longq[kCsrSmallMax];
   __shared__ int32_t buf[kSortSmem];
   const uint32_t tid = threadIdx.x;
+  if (recheck) recheck_pairs(rc, tid >> 5, blockDim.x >> 5, (int)(tid & 31u));
   if (tid <= B) {
     cnt[tid] = 0u;
     cur[tid] = 0u;
   }
   if (tid == 0) n_long = 0u;
   __syncthreads();
-  const uint32_t n = csr_n(n_cap, n_dev);
+  const uint32_t n = n_dev ? min(__ldcg(n_dev), n_cap) : n_cap;
   for (uint32_t i = tid; i < n; i += blockDim.x) {
     const Pair p = res[i];
     if (p.q < q_lo || p.q - q_lo >= B) {  // not a query of this range: flagged, left out
@@ -2323,25 +2360,17 @@ gt_status ws_reserve_queries(gt_tree *t, int64_t B) {
   cudaFree(w.qbf16);
   cudaFree(w.qn1);
   cudaFree(w.rho);
-  cudaFree(w.thr_keep);
-  cudaFree(w.thr_accept);
   cudaFree(w.bcnt);
   cudaFree(w.boff);
-  w.qf32 = nullptr; w.qbf16 = nullptr; w.qn1 = nullptr; w.rho = nullptr;
-  w.thr_keep = nullptr; w.thr_accept = nullptr; w.q_cap = 0; w.thr_cap = 0;
+  w.qf32 = nullptr; w.qbf16 = nullptr; w.qn1 = nullptr; w.rho = nullptr; w.q_cap = 0;
   w.bcnt = nullptr; w.boff = nullptr;
   GT_CUDA(cudaMalloc(&w.qf32, (size_t)B * t->stride * sizeof(float)));
   GT_CUDA(cudaMalloc(&w.qbf16, (size_t)B * t->stride * sizeof(__nv_bfloat16)));
   GT_CUDA(cudaMalloc(&w.qn1, (size_t)B * sizeof(float)));
   GT_CUDA(cudaMalloc(&w.rho, (size_t)B * sizeof(float)));
-  // the dense GEMM's per-query thresholds (allocated here, never inside a
-  // launch sequence that may be captured into a CUDA graph)
-  GT_CUDA(cudaMalloc(&w.thr_keep, (size_t)B * sizeof(float)));
-  GT_CUDA(cudaMalloc(&w.thr_accept, (size_t)B * sizeof(float)));
   GT_CUDA(cudaMalloc(&w.bcnt, (size_t)(B + 1) * sizeof(int64_t)));
   GT_CUDA(cudaMalloc(&w.boff, (size_t)(B + 1) * sizeof(int64_t)));
   w.q_cap = B;
-  w.thr_cap = B;
   return GT_OK;
 }
 
@@ -2467,7 +2496,7 @@ gt_status ws_reserve_drain(gt_tree *t) {
 static void launch_deferred_bf16(gt_tree *t, cudaStream_t s);
 
 void launch_drain(gt_tree *t, int fmt, int cut, const SibPair *root, const uint32_t *root_count,
-                  cudaStream_t s, uint32_t *level_count, uint32_t *left_count) {
+                  cudaStream_t s, uint32_t *level_count, uint32_t *left_count, bool cleared) {
   Workspace &w = t->ws;
   LevelArgs a;
   std::memset(&a, 0, sizeof(a));
@@ -2499,7 +2528,7 @@ void launch_drain(gt_tree *t, int fmt, int cut, const SibPair *root, const uint3
   a.refine_count = w.counters + kMaxLevels + 2;
   const bool defer = defer_active(t, fmt);
   if (defer) {
-    cudaMemsetAsync(w.counters + kDeferSlot, 0, sizeof(uint32_t), s);
+    if (!cleared) cudaMemsetAsync(w.counters + kDeferSlot, 0, sizeof(uint32_t), s);
     a.defer = w.defer;
     a.defer_count = w.counters + kDeferSlot;
     a.defer_cap = (uint32_t)w.defer_cap;
@@ -2520,7 +2549,7 @@ void launch_drain(gt_tree *t, int fmt, int cut, const SibPair *root, const uint3
   g.scratch = reinterpret_cast<SibPair *>(w.drain);
   g.wcap = 32u << (cut - 1);
   g.cut = cut;
-  cudaMemsetAsync(g.head, 0, sizeof(uint32_t), s);
+  if (!cleared) cudaMemsetAsync(g.head, 0, sizeof(uint32_t), s);
   const bool wide = kv_for<GT_F32>(t->d) != 1024 / (32 * 4);
   if (fmt == GT_BF16)
     wide ? launch_drain_t<GT_BF16, 8>(a, g, t->sm_count, s) : launch_drain_t<GT_BF16, 4>(a, g, t->sm_count, s);
@@ -2860,18 +2889,31 @@ bool items_sub_available(gt_tree *t, int fmt) {
   return ring_depth((int)((t->d * entry_bytes(fmt) + 15) / 16), &slot) > 0;
 }
 
-void launch_recheck(gt_tree *t, int64_t /*q0*/, cudaStream_t s, int max_blocks) {
+static RecheckArgs recheck_args(gt_tree *t) {
   Workspace &w = t->ws;
+  RecheckArgs a;
+  a.rchk = w.rchk;
+  a.count = w.counters + kMaxLevels + 1;
+  a.cap = (uint32_t)w.rchk_cap;
+  a.rows32 = t->rows32;
+  a.stride = t->stride;
+  a.nv4 = (int)((t->d + 3) / 4);
+  a.d_half = t->split_sign ? t->d_in : 0;
+  a.qf32 = w.qf32;
+  a.rho = w.rho;
+  a.res = w.res;
+  a.res_count = w.counters + kMaxLevels;
+  a.res_cap = (uint32_t)w.res_cap;
+  a.q_lim = (uint32_t)w.q_cap;
+  a.n_items = (uint32_t)t->N;
+  a.flags = t->flags;
+  return a;
+}
+
+void launch_recheck(gt_tree *t, int64_t /*q0*/, cudaStream_t s) {
   static int per_sm = 0;
-  // (max_blocks: a smaller grid for a step that rechecks few items, where
-  // scheduling a full grid of blocks that find no work costs more than it)
-  int grid = grid_for((const void *)k_recheck, 256, t->sm_count, per_sm);
-  if (max_blocks > 0) grid = std::min(grid, max_blocks);
-  k_recheck<<<grid, 256, 0, s>>>(w.rchk, w.counters + kMaxLevels + 1, (uint32_t)w.rchk_cap,
-                                 t->rows32, t->stride, (int)((t->d + 3) / 4),
-                                 t->split_sign ? t->d_in : 0, w.qf32, w.rho, w.res,
-                                 w.counters + kMaxLevels, (uint32_t)w.res_cap, (uint32_t)w.q_cap,
-                                 (uint32_t)t->N, t->flags);
+  const int grid = grid_for((const void *)k_recheck, 256, t->sm_count, per_sm);
+  k_recheck<<<grid, 256, 0, s>>>(recheck_args(t));
 }
 
 // CSR assembly of the result pairs res[0..n) into offsets (B + 1) and ids.
@@ -2881,7 +2923,7 @@ void launch_recheck(gt_tree *t, int64_t /*q0*/, cudaStream_t s, int max_blocks) 
 // (clamped to n), so the work can be enqueued before the count is known.
 void launch_csr_into(gt_tree *t, const Pair *res, uint32_t n, const uint32_t *n_dev, int64_t q_lo,
                      int64_t B, int64_t *cnt, int64_t *off, int32_t *ids, uint32_t *list_n,
-                     cudaStream_t s) {
+                     cudaStream_t s, bool recheck) {
   const bool any = n > 0;
   const int blocks = n_dev ? t->sm_count * 4
                            : (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, t->sm_count * 8));
@@ -2890,11 +2932,12 @@ void launch_csr_into(gt_tree *t, const Pair *res, uint32_t n, const uint32_t *n_
   int64_t *cnt_r = cnt + q_lo, *off_r = off + q_lo;
   const uint32_t q_hi = (uint32_t)(q_lo + B);
   if (B >= 1 && B <= kCsrSmallMax) {
-    // one block for the CSR of a few queries
+    // one block for the CSR of a few queries (and, asked to, their recheck)
     k_csr_small<<<1, 1024, 0, s>>>(res, n, n_dev, (uint32_t)q_lo, (uint32_t)B, off_r, t->perm, ids,
-                                   t->flags);
+                                   t->flags, recheck_args(t), recheck ? 1 : 0);
     return;
   }
+  if (recheck) launch_recheck(t, 0, s);
   if (any) k_csr_count<<<blocks, 256, 0, s>>>(res, n, n_dev, (uint32_t)q_lo, q_hi, cnt, t->flags);
   k_scan<<<1, 1024, 0, s>>>(cnt_r, B, off_r);
   cudaMemsetAsync(cnt_r, 0, (size_t)(B + 1) * sizeof(int64_t), s);
