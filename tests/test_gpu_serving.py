@@ -238,6 +238,43 @@ def test_insert_into_a_tail_pool_gives_no_lower_bound(gt, schedule):
     t.close()
 
 
+@pytest.mark.parametrize("schedule", ["levels", "drain", "immediate"])
+@pytest.mark.parametrize("dtype", ["bf16", "fp8"])
+def test_served_recheck_decides_items_at_rho(gt, schedule, dtype):
+    # items one FP32 ulp either side of rho, and rho itself, among 2048: every
+    # bound straddles rho for them, so the FP64 recheck decides them, here in
+    # the served steps of a group of 5 queries (the immediate schedule runs a
+    # small group's recheck in the block that then assembles its CSR)
+    rho = np.float32(0.8)
+    up, dn = np.nextafter(rho, np.float32(2)), np.nextafter(rho, np.float32(0))
+    rng = np.random.default_rng(3)
+    x = np.array([up, dn, rho] * 30 + [0.1] * 1958, dtype=np.float32)[rng.permutation(2048)]
+    F = np.zeros((x.size, 16), np.float32)
+    F[:, 0] = x
+    F[:, 1] = np.sqrt(1 - x.astype(np.float64) ** 2).astype(np.float32)
+    Q = np.zeros((5, 16), np.float32)
+    Q[:, 0] = 1.0                                   # q.f_i = x_i exactly
+    ref = oracle.brute_force(F, Q[:1], np.array([rho]), margin=0.0)
+    assert len(ref.ids) == 60
+    t = gt.Tree(F)
+    srv = gt.Server(t, dtype=dtype, schedule=schedule, max_group=5)
+    srv.submit(Q, np.full(5, rho, np.float32), np.arange(5))
+    got = {}
+    for _ in range(40):
+        srv.step()
+        for tag, ids, snap in srv.poll():
+            got[tag] = ids
+        if len(got) == 5:
+            break
+    st = srv.stats()
+    srv.close()
+    t.close()
+    assert sorted(got) == list(range(5))
+    for i in range(5):
+        assert np.array_equal(got[i], ref.neighbours(0))
+    assert st["rechecks"] >= 5 * 90
+
+
 def test_served_equals_alone(gt, stream_ds):
     ds = stream_ds
     n0 = 40_000
