@@ -758,8 +758,10 @@ def main():
     clocks = Clocks()
     clocks.start()
     clocks.wait_ready()
+    # (the warm-up calls take the timed calls' options, so the CUDA graph the
+    # timed steps replay is captured here, not inside the first timed step)
     for _ in range(a.warmup):
-        step().free()
+        step(timing=True).free()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
