@@ -1014,7 +1014,8 @@ def main():
                   "oracle_ambiguous": int(bf.ambiguous.sum()),
                   "brute_force_seconds": round(bf.seconds, 2),
                   "algorithm1": {"queries": int(len(qs)), "identical": bool(ok_alg1),
-                                 "decisions_outside_its_rounding_bound": int(ref.ambiguous.sum())}}
+                                 # decisions inside its FP64 rounding bound
+                                 "ambiguous_decisions": int(ref.ambiguous.sum())}}
 
     # the serving run inserts rows, so it comes after every exactness check
     served_fixed = None

@@ -26,7 +26,9 @@
  *
  * orc_alg1 additionally carries a rigorous bound on the FP64 rounding error
  * of every score it derives (prefix sums of up to N terms, the difference of
- * two of them, the dot product, and the subtractions of Algorithm 1).  A
+ * two of them, the dot product, and the subtractions of Algorithm 1; the
+ * prefix sums' errors enter a score only through its pool's two ends, see
+ * pool_dot).  A
  * neighbour flag raised or withheld with |sim - rho| inside that bound, or a
  * pool pruned while its exact score could still reach rho + margin (the
  * least score a neighbour can have under the input margin), is counted as
@@ -147,27 +149,43 @@ orc_result *orc_brute_force(const float *F, int64_t N, int d, const float *Q,
 typedef struct {
   int64_t si, ei; /* 1-based, inclusive */
   double sim;     /* q^t (pool) */
-  double err;     /* bound on |sim - exact pool score| */
+  double ta, tb;  /* error terms of the running sums at the pool's ends si - 1 and ei */
+  double rr;      /* accumulated rounding of the differences, dots and subtractions */
   int depth;      /* round of binary splitting the pool belongs to */
 } triple;
 
-/* q^t (Fs[b] - Fs[a]) for 0 <= a < b <= N, plus its rounding bound.  Fs[k]
- * is the FP64 running sum of k FP32 rows, so each element carries at most
- * k * 2^-53 relative error; the element difference adds one rounding and
- * the d-term dot product at most (d + 1) * 2^-53 of the magnitude. */
+/* The rounding bound.  Let E_k be the exact sum of the first k FP32 rows and
+ * Fs_k the FP64 running sum.  All terms are >= 0, so elementwise
+ * |Fs_k - E_k| <= gamma_k E_k and, with q >= 0,
+ *   |q^t (Fs_k - E_k)| <= T_k = 1.01 (k + 1) 2^-53 q^t Fs_k.
+ * A direct score q^t (Fs_b - Fs_a) (pool_dot) differs from the exact
+ * q^t (E_b - E_a) by the two ends' terms, T_b + T_a, plus the rounding of the
+ * element differences and of the d-term dot product, at most
+ * 1.01 (d + 3) 2^-53 sum_j q_j |Fs_b[j] - Fs_a[j]|.
+ * A left half scored by subtraction, sim(parent) - sim(right half), shares
+ * the parent's end ei with the right half: the terms q^t (Fs_ei - E_ei) of
+ * the two cancel exactly, so its error is again the running-sum terms of its
+ * own two ends (si - 1 and the split point) plus the roundings accumulated
+ * down the run of subtractions (the parent's, the right half's, and
+ * 2^-53 |lsim| for the subtraction itself).  The running sums' own errors,
+ * the large part at N = 10^6, therefore do not grow along a run of left
+ * halves. */
 static double pool_dot(const double *Fs, int d, const float *q, int64_t b,
-                       int64_t a, double *err) {
+                       int64_t a, double *tb, double *ta, double *rr) {
   const double *hb = Fs + (size_t)b * (size_t)d;
   const double *ha = Fs + (size_t)a * (size_t)d;
-  double dot = 0.0, mag = 0.0, adot = 0.0;
+  double dot = 0.0, adot = 0.0, qb = 0.0, qa = 0.0;
   for (int j = 0; j < d; ++j) {
     double diff = hb[j] - ha[j];
     dot += (double)q[j] * diff;
     adot += (double)q[j] * fabs(diff);
-    mag += (double)q[j] * (hb[j] + ha[j]);
+    qb += (double)q[j] * hb[j];
+    qa += (double)q[j] * ha[j];
   }
   const double u = ldexp(1.0, -53);
-  *err = 1.01 * u * ((double)(a + b + 2) * mag + (double)(d + 3) * adot);
+  *tb = 1.01 * u * (double)(b + 1) * qb;
+  *ta = 1.01 * u * (double)(a + 1) * qa;
+  *rr = 1.01 * u * (double)(d + 3) * adot;
   return dot;
 }
 
@@ -233,32 +251,35 @@ orc_result *orc_index_query(const orc_index *ix, const float *Q, int64_t B,
       int top = 0;
       double e;
       /* push {1, N, q^t Fs_N} */
-      double s0 = pool_dot(Fs, d, q, N, 0, &e);
+      double tb, ta, rr;
+      double s0 = pool_dot(Fs, d, q, N, 0, &tb, &ta, &rr);
       ++tests;
       ++my_rounds[0];
-      S[top++] = (triple){1, N, s0, e, 0};
+      S[top++] = (triple){1, N, s0, ta, tb, rr, 0};
       while (top > 0) {
         triple t = S[--top];
+        const double terr = t.ta + t.tb + t.rr; /* bound on |t.sim - exact| */
         if (t.sim >= r) {
           int64_t n = t.ei - t.si + 1;
           if (n > 2) {
             int64_t h = n / 2;
             /* right half [si + h, ei]: q^t (Fs_ei - Fs_{si+h-1}) */
-            double er;
-            double rsim = pool_dot(Fs, d, q, t.ei, t.si + h - 1, &er);
+            double rtb, rta, rrr;
+            double rsim = pool_dot(Fs, d, q, t.ei, t.si + h - 1, &rtb, &rta, &rrr);
             ++tests;
             if (t.depth + 1 < MAX_ROUNDS) ++my_rounds[t.depth + 1];
             double lsim = t.sim - rsim;
-            double el = t.err + er + u * fabs(lsim);
-            S[top++] = (triple){t.si + h, t.ei, rsim, er, t.depth + 1};
-            S[top++] = (triple){t.si, t.si + h - 1, lsim, el, t.depth + 1};
+            S[top++] = (triple){t.si + h, t.ei, rsim, rta, rtb, rrr, t.depth + 1};
+            S[top++] = (triple){t.si, t.si + h - 1, lsim, t.ta, rta,
+                                t.rr + rrr + u * fabs(lsim), t.depth + 1};
           } else if (n == 2) {
-            double er;
-            double rsim = pool_dot(Fs, d, q, t.ei, t.si, &er);
+            double rtb, rta, rrr;
+            double rsim = pool_dot(Fs, d, q, t.ei, t.si, &rtb, &rta, &rrr);
             ++tests;
             if (t.depth + 1 < MAX_ROUNDS) ++my_rounds[t.depth + 1];
             double lsim = t.sim - rsim;
-            double el = t.err + er + u * fabs(lsim);
+            double er = rta + rtb + rrr;
+            double el = t.ta + rta + t.rr + rrr + u * fabs(lsim);
             if (rsim >= r) ivec_push(&out, (int32_t)(t.ei - 1));
             if (fabs(rsim - r) <= er) ++amb;
             if (lsim >= r) ivec_push(&out, (int32_t)(t.si - 1));
@@ -266,11 +287,11 @@ orc_result *orc_index_query(const orc_index *ix, const float *Q, int64_t B,
           } else {
             /* a single item whose (derived) score passed */
             ivec_push(&out, (int32_t)(t.si - 1));
-            if (fabs(t.sim - r) <= t.err) ++amb;
+            if (fabs(t.sim - r) <= terr) ++amb;
           }
         } else if (t.ei == t.si) {
-          if (fabs(t.sim - r) <= t.err) ++amb; /* an item withheld inside the bound */
-        } else if (t.sim + t.err >= r + margin) {
+          if (fabs(t.sim - r) <= terr) ++amb; /* an item withheld inside the bound */
+        } else if (t.sim + terr >= r + margin) {
           /* a pruned pool could hold a neighbour only if its exact score
            * reached rho + margin (all member scores are >= 0) */
           ++amb;

@@ -143,6 +143,65 @@ def test_alg1_equals_brute_force_workload(small_ds):
     assert a.tests.min() >= 1 and a.tests.max() <= ds.F.shape[0]
 
 
+def test_alg1_bound_flags_a_tie_deep_in_the_array():
+    # an item scoring exactly rho at position 3001 of 4096: its score is
+    # derived from running sums with a nonzero error bound, so the decision
+    # is counted as ambiguous (a bound of zero, or one dropping the running
+    # sums' terms, would report none)
+    rho = np.float32(0.8)
+    x = np.full(4096, 0.1, np.float32)
+    x[3001] = rho
+    F, q = _two_hot(x)
+    a = oracle.Index(F).query(q, rho, margin=0.0)
+    assert a.ambiguous.sum() >= 1
+    assert 3001 in a.neighbours(0).tolist()        # the FP64 sums here are exact
+
+
+def test_alg1_bound_covers_large_running_sums():
+    # 1000 items of about 1e9 first, then about a million items scoring
+    # 0.01-0.1 (full FP32 mantissas): the running sums are about 1e12, so
+    # every addition rounds by up to 6e-5, and items one FP32 ulp either side
+    # of rho deep in the array get derived scores that can fall on the wrong
+    # side of rho.  The bound's running-sum terms (about 0.1 there) flag each
+    # of them; decisions on items far from rho stay exact.
+    rng = np.random.default_rng(11)
+    rho = np.float32(0.8)
+    near = np.array([300_017, 555_555, 777_001, 999_983])
+    x = np.concatenate([rng.uniform(1e9, 2e9, 1000),
+                        rng.uniform(0.01, 0.1, 1_000_000)]).astype(np.float32)
+    x[near[0::2]] = np.nextafter(rho, np.float32(2))
+    x[near[1::2]] = np.nextafter(rho, np.float32(0))
+    F = np.zeros((x.size, 2), np.float32)
+    F[:, 0] = x
+    q = np.array([[1.0, 0.0]], np.float32)
+    a = oracle.Index(F).query(q, rho, margin=0.0)
+    assert a.ambiguous.sum() >= near.size
+    exact = np.nonzero(x >= rho)[0]                   # q.f_i = x_i exactly
+    got = a.neighbours(0)
+    assert np.array_equal(np.setdiff1d(got, near), np.setdiff1d(exact, near))
+
+
+def test_alg1_bound_at_full_scale():
+    # N = 1M, d = 1000 softmax features, rho = 0.8: the queries of the
+    # benchmark's 1024-query sample on which a bound that adds the parent's
+    # whole error at every subtraction (so that the running sums' errors grow
+    # down a run of left halves) reported decisions it could not vouch for.
+    # Their errors cancel at the shared end of a pool and its right half, so
+    # every decision is vouched for, and the sets equal the brute force.
+    import synth
+    qs = np.array([216, 229, 350, 358, 1025, 1752, 1756, 2305, 4042, 4656, 5399, 6240,
+                   6293, 6517, 7226, 7572, 8001, 8943, 8992, 9916])
+    ds = synth.generate("softmax_n1m_d1000", screen=qs, device="cpu")
+    rho = ds.rho_for(0.8)[qs]
+    ix = oracle.Index(ds.F)
+    a = ix.query(ds.Q[qs], rho)
+    ix.close()
+    b = oracle.brute_force(ds.F, ds.Q[qs], rho)
+    assert b.ambiguous.sum() == 0
+    assert a.ambiguous.sum() == 0
+    assert np.array_equal(a.offsets, b.offsets) and np.array_equal(a.ids, b.ids)
+
+
 # -- pooling by element-wise maximum (Sec. 2) --------------------------------------
 
 def _split_path_depth(N, t):
