@@ -17,6 +17,7 @@ the tree (queries are independent: weak scaling, no data-path collective).
 from __future__ import annotations
 
 import argparse
+import gc
 import hashlib
 import json
 import os
@@ -770,14 +771,22 @@ def main():
     stats = []
     torch.cuda.synchronize()
     clocks.mark()
-    for i in range(a.steps):
-        flush.zero_()                       # L2 flush, outside the timed events
-        ev[i][0].record(stream)
-        r = step(timing=True)
-        ev[i][1].record(stream)
-        stats.append(r.stats)
-        r.free()
-    torch.cuda.synchronize()
+    # (Python's cyclic collector is paused over the timed steps, as timeit
+    # does: a collection inside a step would time the interpreter, not the
+    # library)
+    gc.collect()
+    gc.disable()
+    try:
+        for i in range(a.steps):
+            flush.zero_()                       # L2 flush, outside the timed events
+            ev[i][0].record(stream)
+            r = step(timing=True)
+            ev[i][1].record(stream)
+            stats.append(r.stats)
+            r.free()
+        torch.cuda.synchronize()
+    finally:
+        gc.enable()
     clk = clocks.stop(local)
     step_ms = [s.elapsed_time(e) for s, e in ev]
     total_ms = reduce_max(sum(step_ms), dist)
